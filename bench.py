@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the Heisenberg spin-glass Monte Carlo on one B300 (or N, as
+independent replicas): spin updates/ns of the batched FP16-coupling form,
+with the plain FP32 form, the HBM roofline fraction of the dominant kernel,
+an end-to-end figure through the public API from host buffers, and the FP64
+oracle on the host cores as a CPU baseline.
+
+Workload (default): L = 64, 8 disorder samples per GPU, 32 temperatures evenly
+spaced in [0.15, 0.75] x 2 replicas (64 lattices per sample, 512 per GPU),
+Gaussian couplings quantised to FP16, FP32 spins.  One Monte Carlo step (MCS)
+is 1 heat-bath sweep + 8 overrelaxation sweeps + energies + one PT sweep; the
+observables are measured every 10 MCS.  One bench step = 10 MCS, so every
+step runs every stage of the path.  The spins (1.6 GB per GPU) exceed L2, so
+no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hsg|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin updates/ns and % HBM roofline, batched FP16-coupling vs plain FP32 (1 B300)"
+UNIT = "spin updates/ns"
+MCS_PER_STEP = 10
+
+WORKLOADS = {
+    "L64_S8_R64_f16": dict(L=64, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
+                           measure_every=10),
+    "L32_S64_R48_f16": dict(L=32, S=64, n_rep=2, NT=24, Tmin=0.15, Tmax=0.75, n_or=8,
+                            measure_every=10),
+    # profiling size: 512 lattices of L=32 (201 MB of spins, above L2)
+    "L32_S8_R64_f16": dict(L=32, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
+                           measure_every=10),
+}
+DEFAULT_WORKLOAD = "L64_S8_R64_f16"
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by a
+# hash of the kernel sources the capture was taken with (stale -> null).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "philox.cuh", "hsg.cu"):
+        with open(os.path.join(ROOT, "paper_1309_1599_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def b_alg(R_share: int, bond_bytes: int) -> float:
+    """Algorithmic bytes per site update: each spin (12 B) read and written
+    once per sweep, each bond's bond_bytes read once per sweep for all
+    R_share lattices that share it (3 bonds per site)."""
+    return 2 * 12 + 3 * bond_bytes / R_share
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing
+# ----------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    def __init__(self, world, rank, local, backend):
+        import torch
+        self.world, self.rank, self.local = world, rank, local
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+        self.torch = torch
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64,
+                              device="cuda" if self.torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# inputs
+# ----------------------------------------------------------------------------
+def make_inputs(w, rank, seed=1):
+    import hsg_inputs as gi
+    L, S, R = w["L"], w["S"], w["n_rep"] * w["NT"]
+    samples = [rank * S + s for s in range(S)]
+    J = [gi.couplings(L, seed, sg, precision="f16") for sg in samples]
+    spins = [[gi.random_spins(L, seed, sg, j) for j in range(R)] for sg in samples]
+    beta = gi.linear_betas(w["Tmin"], w["Tmax"], w["NT"])
+    return samples, J, spins, beta
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# the hsg arm
+# ----------------------------------------------------------------------------
+def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1):
+    lat = hsg.Lattice([w["L"]] * len(samples), beta, n_replicas=w["n_rep"], coupling_prec=prec,
+                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed)
+    for s in range(len(samples)):
+        lat.set_couplings(s, J[s])
+        for j in range(lat.R):
+            lat.set_spins(s, j, spins[s][j])
+    return lat
+
+
+def time_steps(lat, steps, torch, dist, sampler=None):
+    """Device time of `steps` bench steps (10 MCS each), CUDA events on the
+    stream the library launches on, barrier + synchronize on both sides."""
+    stream = torch.cuda.current_stream()
+    dist.barrier()
+    torch.cuda.synchronize()
+    l0 = lat.get_launch_count()
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        lat.run_steps(MCS_PER_STEP)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    dist.barrier()
+    ms = e0.elapsed_time(e1)
+    return ms, lat.get_launch_count() - l0, clocks
+
+
+def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
+    """Average duration of one overrelaxation half-sweep launch (the dominant
+    kernel), from CUDA events around sweep_or calls on the library's stream."""
+    stream = torch.cuda.current_stream()
+    lat.sweep_or(sweeps)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_calls):
+        lat.sweep_or(sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (n_calls * 2 * sweeps)
+
+
+def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak):
+    samples, J, spins, beta = inputs
+    lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout)
+    N, R, S = w["L"] ** 3, lat.R, len(samples)
+    for _ in range(warmup):
+        lat.run_steps(MCS_PER_STEP)
+    torch.cuda.synchronize()
+    ms, launches, clocks = time_steps(lat, steps, torch, dist, sampler)
+    ms_max = dist.max(ms)
+    updates_rank = S * R * N * (1 + w["n_or"]) * MCS_PER_STEP * steps
+    value = updates_rank * dist.world / (ms_max * 1e6)
+    or_ms = time_or_kernel(lat, torch)
+    bond_bytes = 12 if prec == hsg.F16 else 24
+    r_share = R if layout == hsg.BATCHED else 1
+    balg = b_alg(r_share, bond_bytes)
+    bytes_launch = S * R * (N // 2) * balg
+    achieved = bytes_launch / (or_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_sweep_half<OR,{2 if layout == hsg.BATCHED else 1},"
+                                      f"{'f16' if prec == hsg.F16 else 'f32'}>",
+            "achieved": round(achieved, 1), "peak": peak[0], "peak_source": peak[1],
+            "unit": "GB/s", "frac": round(achieved / peak[0], 4),
+            "b_alg_bytes_per_update": round(balg, 4),
+            "bytes_per_launch": int(bytes_launch), "launch_ms": round(or_ms, 4),
+            "updates_per_ns_roofline": round(peak[0] / balg, 2),
+            "traffic": None}
+    key = (kernel_source_hash(), roof["kernel"])
+    if key in NCU_TRAFFIC:
+        roof["traffic"] = NCU_TRAFFIC[key]
+    out = dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
+               roofline=roof, lat=lat)
+    return out
+
+
+def e2e_run(hsg, torch, dist, w, inputs, steps):
+    """Whole job through the public API from pinned host buffers: couplings and
+    initial spins host->device, `steps` bench steps, observables and final
+    spins device->host.  Wall time around it, synchronised."""
+    samples, J, spins, beta = inputs
+    L, S = w["L"], len(samples)
+    lat = hsg.Lattice([L] * S, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
+                      layout=hsg.BATCHED, n_or=w["n_or"], measure_every=w["measure_every"])
+    R, N = lat.R, L ** 3
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    J_h = [pin(j) for j in J]
+    s_h = [[pin(x) for x in row] for row in spins]
+    out_h = [[torch.empty((N, 3), dtype=torch.float32).pin_memory() for _ in range(R)]
+             for _ in range(S)]
+    lat.run_steps(1)                   # capture graphs outside the timed region
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for s in range(S):
+        lat.set_couplings(s, J_h[s].numpy())
+        for j in range(R):
+            lat.set_spins(s, j, s_h[s][j])
+    for _ in range(steps):
+        lat.run_steps(MCS_PER_STEP)
+    obs, counts = lat.read_observables()
+    for s in range(S):
+        for j in range(R):
+            lat.get_spins(s, j, out=out_h[s][j])
+    torch.cuda.synchronize()
+    dt = dist.max(time.perf_counter() - t0)
+    lat.destroy()
+    updates = S * R * N * (1 + w["n_or"]) * MCS_PER_STEP * steps * dist.world
+    h2d = sum(x.numel() * 4 for x in J_h) + S * R * N * 12
+    d2h = obs.nbytes + counts.nbytes + S * R * N * 12
+    return {"value": updates / (dt * 1e9), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
+            "wall_s": round(dt, 3)}
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_sample_run(w, inputs, n_mcs, threads):
+    """The FP64 oracle on one sample (R lattices) of the workload for n_mcs
+    Monte Carlo steps; returns (updates, seconds)."""
+    import oracle
+    samples, J, spins, beta = inputs
+    smp = oracle.Sample(w["L"], J[0], np.stack(spins[0]), beta, w["n_rep"], 1,
+                        sample_index=samples[0])
+    t0 = time.perf_counter()
+    smp.run(n_mcs, w["n_or"], w["measure_every"], n_threads=threads)
+    dt = time.perf_counter() - t0
+    return smp.R * w["L"] ** 3 * (1 + w["n_or"]) * n_mcs, dt
+
+
+def cpu_baseline(w, inputs, budget_s=15.0):
+    threads = os.cpu_count() or 1
+    ups, dt = oracle_sample_run(w, inputs, 1, threads)
+    n = 1
+    while dt < budget_s / 3 and n < 64:
+        more = max(1, int(n * (budget_s / max(dt, 1e-3) - 1)))
+        u2, d2 = oracle_sample_run(w, inputs, more, threads)
+        ups, dt, n = ups + u2, dt + d2, n + more
+    return {"value": ups / (dt * 1e9), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} MCS of 1 sample ({w['n_rep'] * w['NT']} lattices of L={w['L']}, "
+                      f"FP16-quantised couplings as FP64), OpenMP over lattices, "
+                      f"{dt:.1f} s"}
+
+
+def reference_arm(args, w, world, rank, local):
+    if rank != 0:
+        return 0
+    inputs = make_inputs(w, 0)
+    threads = os.cpu_count() or 1
+    times, ups = [], 0
+    for i in range(args.warmup + args.steps):
+        u, dt = oracle_sample_run(w, inputs, 1, threads)
+        if i >= args.warmup:
+            times.append(dt)
+            ups += u
+    total = sum(times)
+    value = ups / (total * 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "step": "1 MCS of 1 sample (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
+                             "sample": "each step: 1 MCS of sample 0 (64 lattices of L=64)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hsg", choices=["hsg", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, w, world, rank, local)
+
+    import torch
+    import paper_1309_1599_b300 as hsg
+    torch.cuda.set_device(local)
+    dist = Dist(world, rank, local, "nccl")
+    peak = measured_peaks()
+    inputs = make_inputs(w, rank)
+
+    sampler = ClockSampler(local)
+    batched = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
+                       args.warmup, sampler, peak)
+    batched["lat"].destroy()
+    plain = None
+    if not args.no_plain:
+        plain = run_form(hsg, torch, dist, w, inputs, hsg.F32, hsg.PLAIN, args.steps,
+                         args.warmup, None, peak)
+        plain["lat"].destroy()
+    e2e = None if args.no_e2e else e2e_run(hsg, torch, dist, w, inputs, args.steps)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, inputs)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(batched["value"], 3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(batched["ms_per_step"], 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "L": w["L"], "samples_per_gpu": w["S"],
+                           "lattices_per_sample": w["n_rep"] * w["NT"], "n_temps": w["NT"],
+                           "T_range": [w["Tmin"], w["Tmax"]], "n_or": w["n_or"],
+                           "couplings": "gaussian, FP16-quantised", "layout": "batched",
+                           "step": f"{MCS_PER_STEP} MCS (HB + {w['n_or']} OR + PT each) + 1 measurement",
+                           "l2": "no flush: spins per GPU exceed L2 (126 MB)",
+                           "parallelism": f"replicas x{world} (independent samples per GPU)"},
+                "roofline": batched["roofline"], "gpu_launches": batched["launches"],
+                "clocks": batched["clocks"], "e2e": e2e, "cpu_baseline": cpu}
+        if plain is not None:
+            line["plain_fp32"] = {"value": round(plain["value"], 3),
+                                  "ms_per_step": round(plain["ms_per_step"], 3),
+                                  "roofline": plain["roofline"], "gpu_launches": plain["launches"]}
+            line["batched_over_plain"] = round(batched["value"] / plain["value"], 3)
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

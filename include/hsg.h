@@ -1,0 +1,206 @@
+/*
+ * hsg.h -- C ABI of libhsg: equilibrium Monte Carlo of the 3d Edwards-Anderson
+ * Heisenberg spin glass with random anisotropic couplings on one NVIDIA B300
+ * (Baity-Jesi, Fernandez, Martin-Mayor, Sanz, arXiv:1309.1599).
+ *
+ * Model (Sec. II.A, Eq. (1)): unit 3-vector spins s_x on a periodic L^3 cubic
+ * lattice, H = -sum_<x,y> s_x^T J_xy s_y, J_xy = eps_xy I + D_xy with D
+ * symmetric, so every bond carries a symmetric 3x3 matrix of six entries.
+ * A "sample" is one realisation of the couplings; it is simulated as
+ * R = n_replicas * n_temps lattices ("slots") sharing those couplings.
+ * Slot j of a sample is replica j / n_temps; at creation it sits at
+ * temperature index j % n_temps.  Parallel tempering exchanges temperature
+ * labels, never spins (App. A.1).
+ *
+ * Conventions for every call:
+ *   - site index i = x + L*(y + L*z), 0 <= x,y,z < L; black sites have x+y+z
+ *     even, white sites odd; a sweep updates all black sites, then all white.
+ *   - Host arrays are owned by the caller and are read or written before the
+ *     call returns.  All device memory is owned by the library.
+ *   - Compute calls (sweeps, energies, PT, measurement, run_steps) are
+ *     asynchronous: they are enqueued on the configured CUDA stream and return
+ *     at once.  Calls that move data to or from the host synchronise that
+ *     stream first.
+ *   - Every call returns an hsg_status.  HSG_EINVAL leaves the state
+ *     unchanged.  A CUDA failure returns HSG_ECUDA; a device-side wait that
+ *     gave up returns HSG_ETIMEOUT.  hsg_last_error() describes the last
+ *     failure of the calling thread.  Nothing aborts the process or traps the
+ *     GPU.
+ *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed mod 2^32, seed >> 32); they replace the generator of App. A.4.
+ *       heat-bath draw at site i of lattice l (l = sample*R + slot) in
+ *       heat-bath sweep t: counter (i, l/2, t, 1); even l uses output words
+ *       0,1, odd l words 2,3; uniform r = ((w >> 9) + 1/2) * 2^-23.
+ *       parallel-tempering pair k of replica set g (g = sample*n_replicas + r)
+ *       in PT sweep t: counter (k, g, t, 2); r = (((w0>>6)<<26 | w1>>6) + 1/2)
+ *       * 2^-52.
+ *     The library keeps the sweep counters t on the device; they start at 0.
+ */
+#ifndef HSG_H
+#define HSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsg_ctx *hsg_t;
+
+typedef enum {
+  HSG_OK = 0,
+  HSG_EINVAL = 1,   /* bad argument or configuration; nothing changed */
+  HSG_ENOMEM = 2,   /* device or host allocation failed */
+  HSG_ECUDA = 3,    /* a CUDA runtime call or kernel failed */
+  HSG_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  HSG_ESTATE = 5,   /* call not valid in the current state */
+  HSG_EIO = 6       /* checkpoint file could not be read or written */
+} hsg_status;
+
+/* Storage precision of the couplings on the device.  Values are rounded once
+ * (round to nearest even) from the float32 host array. */
+enum { HSG_F32 = 0, HSG_F16 = 1 };
+
+/* Device spin layout.
+ *   HSG_LAYOUT_PLAIN    one lattice per thread; each lattice reads its own
+ *                       couplings (the plain single-lattice form).
+ *   HSG_LAYOUT_BATCHED  two lattices of the same sample interleaved per
+ *                       element, updated by one thread against one coupling
+ *                       read (requires R even). */
+enum { HSG_LAYOUT_PLAIN = 0, HSG_LAYOUT_BATCHED = 1 };
+
+/* Observables accumulated per (sample, temperature index) by hsg_measure
+ * (Sec. II.B).  Per measurement, with e = E/N:
+ *   [0] sum of e, [1] sum of e^2      over the n_replicas lattices at that T
+ *   [2] |q(0)|^2, [3] |q(0)|^4, [4] mean_nu |q(k_nu)|^2,
+ *   [5] mean_mu |qCG^mu(0)|^2, [6] mean_mu |qCG^mu(0)|^4,
+ *   [7] mean_{mu,nu} |qCG^mu(k_nu)|^2  summed over replica pairs (0,1),(2,3),...
+ *   [8] sum of the Schwinger-Dyson residual (1/N) sum_x [2T s.h - h^2 + (s.h)^2]
+ *       over the lattices at that T (App. A.4.3; 0 where beta = 0)
+ * where q(k) = sum_x s^a_x.s^b_x e^{ik.x}/N, k_nu = (2 pi/L) e_nu, and
+ * qCG^mu(k) is the same sum of zeta^a_{x,mu} zeta^b_{x,mu}, zeta_{x,mu} =
+ * s_{x+mu}.(s_x x s_{x-mu}).  counts[] holds the number of measurements. */
+enum { HSG_NOBS = 9 };
+
+typedef struct {
+  int n_samples;          /* S >= 1 */
+  const int *L;           /* [S] linear sizes, each even, 4 <= L <= 512 */
+  int n_replicas;         /* >= 1 */
+  int n_temps;            /* N_T >= 1 */
+  const double *beta;     /* [N_T] inverse temperatures, >= 0, increasing */
+  int coupling_prec;      /* HSG_F32 or HSG_F16 */
+  int layout;             /* HSG_LAYOUT_PLAIN or HSG_LAYOUT_BATCHED */
+  int n_or;               /* overrelaxation sweeps per step, >= 0 */
+  int measure_every;      /* hsg_run_steps measures every this many steps (0: never) */
+  uint64_t seed;          /* Philox key */
+  void *stream;           /* cudaStream_t to use; NULL = the legacy default stream */
+  long long timeout_cycles; /* bound for device-side waits, 0 = library default */
+} hsg_config;
+
+/* Create a context: validates cfg (copied; the caller's arrays may be freed
+ * afterwards), allocates all device buffers on the current CUDA device, sets
+ * every coupling to 0 and every spin to (0,0,1), the temperature labels to
+ * the identity and all counters and accumulators to 0.  *out receives the
+ * handle (NULL on failure). */
+hsg_status hsg_lattice_create(const hsg_config *cfg, hsg_t *out);
+
+/* Release every resource of h (NULL is ignored).  Synchronises its stream. */
+void hsg_destroy(hsg_t h);
+
+/* Couplings of one sample from host float32 [N][3][6]: entry [i][mu][e] is
+ * element e = (xx,yy,zz,xy,xz,yz) of the symmetric matrix on the bond
+ * (i, i+e_mu), mu = 0,1,2 = +x,+y,+z.  Rounded once to the storage precision.
+ * Invalidates the stored energies. */
+hsg_status hsg_set_couplings(hsg_t h, int sample, const float *J6);
+
+/* The stored couplings of one sample as float32 [N][3][6] (exact values). */
+hsg_status hsg_get_couplings(hsg_t h, int sample, float *J6_out);
+
+/* Spins of one lattice slot from / to host float32 [N][3].  Spins are stored
+ * as given (no normalisation). */
+hsg_status hsg_set_spins(hsg_t h, int sample, int slot, const float *s);
+hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float *s_out);
+
+/* n checkerboard sweeps of every lattice (App. A.1): heat-bath draws from
+ * P(s) ~ exp(beta s.h) at each lattice's current temperature; overrelaxation
+ * reflects s about h, s' = 2h(h.s)/h^2 - s (unchanged where h = 0).  Each
+ * heat-bath sweep advances the heat-bath counter by one.  The last
+ * overrelaxation sweep also leaves the energies current. */
+hsg_status hsg_sweep_hb(hsg_t h, int n);
+hsg_status hsg_sweep_or(hsg_t h, int n);
+
+/* Recompute the energy E = -sum_bonds s_x^T J s_y (Eq. (1)) of every lattice
+ * (FP32 terms, FP64 sums). */
+hsg_status hsg_energy(hsg_t h);
+
+/* Energies of all lattices, double [S][R] by slot (computed first if stale). */
+hsg_status hsg_get_energies(hsg_t h, double *E_out);
+
+/* Overwrite the stored energies (double [S][R]); used to drive hsg_pt_swap
+ * with chosen values.  They stay current until the next sweep. */
+hsg_status hsg_set_energies(hsg_t h, const double *E);
+
+/* One parallel-tempering sweep of every replica set (App. A.1): pairs of
+ * neighbouring temperature indices k = 0 .. N_T-2 in order; the exchange of
+ * labels k, k+1 is accepted iff D >= 0 or r < exp(D), D = (beta_k -
+ * beta_{k+1})(E[perm k] - E[perm k+1]) in FP64.  Advances the PT counter. */
+hsg_status hsg_pt_swap(hsg_t h);
+
+/* Temperature labels, int [S][n_replicas][N_T]: the slot at each temperature. */
+hsg_status hsg_get_perm(hsg_t h, int *perm_out);
+hsg_status hsg_set_perm(hsg_t h, const int *perm);
+
+/* Accepted PT exchanges, long long [S][n_replicas][max(N_T-1,1)]. */
+hsg_status hsg_get_pt_accepts(hsg_t h, long long *acc_out);
+
+/* Accumulate one measurement of the observables listed at HSG_NOBS. */
+hsg_status hsg_measure(hsg_t h);
+
+/* n_steps Monte Carlo steps (Sec. III): one heat-bath sweep, n_or
+ * overrelaxation sweeps, the energies, one PT sweep when N_T > 1, and a
+ * measurement after every measure_every-th step (counted over the life of
+ * the context).  Replayed from captured CUDA graphs. */
+hsg_status hsg_run_steps(hsg_t h, int n_steps);
+
+/* Accumulated observables, double [S][N_T][HSG_NOBS], and the number of
+ * measurements, long long [S][N_T] (counts may be NULL). */
+hsg_status hsg_read_observables(hsg_t h, double *obs_out, long long *counts_out);
+hsg_status hsg_reset_observables(hsg_t h);
+
+/* Counters: out[0] heat-bath sweeps, out[1] PT sweeps, out[2] steps.
+ * hsg_set_counters sets all three (for resuming a run elsewhere). */
+hsg_status hsg_get_counters(hsg_t h, uint64_t out[3]);
+hsg_status hsg_set_counters(hsg_t h, const uint64_t in[3]);
+
+/* Number of compute kernels this context has enqueued so far (sweeps,
+ * energies, PT, measurement and counter updates, including those replayed
+ * from graphs; data-transfer helpers are not counted). */
+hsg_status hsg_get_launch_count(hsg_t h, uint64_t *out);
+
+/* Checkpoint: spins, couplings, temperature labels, energies, counters and
+ * accumulators to a binary file, and back into a context created with the
+ * same configuration.  Philox is counter based, so a resumed run is
+ * bit-identical to an uninterrupted one. */
+hsg_status hsg_save(hsg_t h, const char *path);
+hsg_status hsg_load(hsg_t h, const char *path);
+
+/* Wait for all work enqueued by h. */
+hsg_status hsg_synchronize(hsg_t h);
+
+/* Philox4x32-10 evaluated on the device: in = host uint32 [n][6] rows
+ * (c0,c1,c2,c3,k0,k1), out = host uint32 [n][4].  For checking the device
+ * generator against other implementations. */
+hsg_status hsg_philox4x32_10(const uint32_t *in, long n, uint32_t *out);
+
+/* Message of the last failure in the calling thread ("" if none). */
+const char *hsg_last_error(void);
+
+/* ABI version of this header. */
+int hsg_version(void);
+#define HSG_VERSION 1
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSG_H */

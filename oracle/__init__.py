@@ -98,6 +98,7 @@ def _load():
                 "oracle_hb_draw_batch": (None, [vp, d, u64, u32, u32, ctypes.c_long, vp]),
                 "oracle_two_site_chain": (None, [vp, d, u64, u32, ctypes.c_long,
                                                  ctypes.c_long, vp, vp, vp]),
+                "oracle_fields": (None, [i32, vp, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -175,6 +176,14 @@ def local_field(L: int, J9, s, i: int) -> np.ndarray:
     J9, s = _f64(J9), _f64(s)
     h = np.zeros(3)
     _load().oracle_local_field(L, _ptr(J9), _ptr(s), i, _ptr(h))
+    return h
+
+
+def fields(L: int, J9, s, colour: int) -> np.ndarray:
+    """Local fields [N,3] of the sites of one colour (zeros elsewhere)."""
+    J9, s = _f64(J9), _f64(s)
+    h = np.zeros((L ** 3, 3))
+    _load().oracle_fields(L, _ptr(J9), _ptr(s), colour, _ptr(h))
     return h
 
 

@@ -545,3 +545,11 @@ void oracle_two_site_chain(const double J[9], double beta, uint64_t seed,
     }
   }
 }
+
+/* Local fields of every site of one colour: h_out[i*3 + a] for sites of that
+ * colour (other entries untouched). */
+void oracle_fields(int L, const double *J9, const double *s, int colour, double *h_out) {
+  long N = (long)L * L * L;
+  for (long i = 0; i < N; ++i)
+    if (site_colour(L, i) == colour) oracle_local_field(L, J9, s, i, h_out + i * 3);
+}

@@ -1,0 +1,295 @@
+"""Python binding of libhsg (include/hsg.h): Monte Carlo of the 3d
+Heisenberg spin glass with random anisotropic couplings on one B300
+(arXiv:1309.1599).
+
+Argument marshalling only: every step of the Monte Carlo runs in the CUDA
+kernels of ``libhsg.so``.  The binding refuses to work without that library
+or without a CUDA device; there is no CPU fallback.  PyTorch is used only to
+obtain the current CUDA stream.
+
+Method names follow the C functions without the ``hsg_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Lattice", "HsgError", "load_library", "philox4x32_10", "library_path",
+           "F32", "F16", "PLAIN", "BATCHED", "NOBS", "OBS_NAMES"]
+
+F32, F16 = 0, 1
+PLAIN, BATCHED = 0, 1
+NOBS = 9
+OBS_NAMES = ("e", "e2", "q2", "q4", "q2k", "c2", "c4", "c2k", "sd")
+_STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA",
+           4: "HSG_ETIMEOUT", 5: "HSG_ESTATE", 6: "HSG_EIO"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libhsg.so")
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+class HsgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int), ("L", ctypes.POINTER(ctypes.c_int)),
+                ("n_replicas", ctypes.c_int), ("n_temps", ctypes.c_int),
+                ("beta", ctypes.POINTER(ctypes.c_double)), ("coupling_prec", ctypes.c_int),
+                ("layout", ctypes.c_int), ("n_or", ctypes.c_int), ("measure_every", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("timeout_cycles", ctypes.c_longlong)]
+
+
+_SIGNATURES = {
+    "hsg_lattice_create": [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)],
+    "hsg_set_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_set_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "hsg_sweep_hb": [ctypes.c_void_p, ctypes.c_int],
+    "hsg_sweep_or": [ctypes.c_void_p, ctypes.c_int],
+    "hsg_energy": [ctypes.c_void_p],
+    "hsg_get_energies": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_set_energies": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_pt_swap": [ctypes.c_void_p],
+    "hsg_get_perm": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_set_perm": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_get_pt_accepts": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_measure": [ctypes.c_void_p],
+    "hsg_run_steps": [ctypes.c_void_p, ctypes.c_int],
+    "hsg_read_observables": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_reset_observables": [ctypes.c_void_p],
+    "hsg_get_counters": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_set_counters": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_get_launch_count": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_save": [ctypes.c_void_p, ctypes.c_char_p],
+    "hsg_load": [ctypes.c_void_p, ctypes.c_char_p],
+    "hsg_synchronize": [ctypes.c_void_p],
+    "hsg_philox4x32_10": [ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p],
+}
+
+
+def load_library():
+    """Load libhsg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                              "`python paper_1309_1599_b300/build.py` (needs nvcc)")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.hsg_destroy.argtypes = [ctypes.c_void_p]
+        lib.hsg_destroy.restype = None
+        lib.hsg_last_error.argtypes = []
+        lib.hsg_last_error.restype = ctypes.c_char_p
+        lib.hsg_version.argtypes = []
+        lib.hsg_version.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise HsgError(status, load_library().hsg_last_error().decode())
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    """Address of a contiguous numpy array or CPU torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _require_gpu() -> None:
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libhsg needs a CUDA device (B300); none is visible")
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def philox4x32_10(rows) -> np.ndarray:
+    """Device Philox4x32-10 of rows (c0,c1,c2,c3,k0,k1) -> uint32 [n, 4]."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint32).reshape(-1, 6)
+    out = np.empty((rows.shape[0], 4), dtype=np.uint32)
+    _check(load_library().hsg_philox4x32_10(_ptr(rows), rows.shape[0], _ptr(out)))
+    return out
+
+
+class Lattice:
+    """One libhsg context: S samples x n_replicas x n_temps lattices.
+
+    ``Lattice(L, beta, n_replicas, ...)`` is hsg_lattice_create; L is an int
+    or a list of per-sample sizes."""
+
+    def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
+                 layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
+                 timeout_cycles=0):
+        lib = load_library()
+        _require_gpu()
+        if np.isscalar(L):
+            L = [int(L)] * (1 if n_samples is None else int(n_samples))
+        self.Ls = [int(x) for x in L]
+        self.S = len(self.Ls)
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64).reshape(-1)
+        self.NT = len(self.beta)
+        self.n_replicas = int(n_replicas)
+        self.R = self.n_replicas * self.NT
+        self.n_or = int(n_or)
+        self.seed = int(seed) & (2**64 - 1)
+        self._L_arr = (ctypes.c_int * self.S)(*self.Ls)
+        cfg = _Config()
+        cfg.n_samples = self.S
+        cfg.L = self._L_arr
+        cfg.n_replicas = self.n_replicas
+        cfg.n_temps = self.NT
+        cfg.beta = self.beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.coupling_prec = int(coupling_prec)
+        cfg.layout = int(layout)
+        cfg.n_or = self.n_or
+        cfg.measure_every = int(measure_every)
+        cfg.seed = int(seed) & (2**64 - 1)
+        cfg.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
+        cfg.timeout_cycles = int(timeout_cycles)
+        h = ctypes.c_void_p()
+        _check(lib.hsg_lattice_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    # -- lifetime --------------------------------------------------------
+    def destroy(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.hsg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def N(self, sample: int = 0) -> int:
+        return self.Ls[sample] ** 3
+
+    # -- data ------------------------------------------------------------
+    def set_couplings(self, sample: int, J6) -> None:
+        J6 = np.ascontiguousarray(J6, dtype=np.float32)
+        assert J6.size == self.N(sample) * 18
+        _check(self._lib.hsg_set_couplings(self._h, sample, _ptr(J6)))
+
+    def get_couplings(self, sample: int) -> np.ndarray:
+        out = np.empty((self.N(sample), 3, 6), dtype=np.float32)
+        _check(self._lib.hsg_get_couplings(self._h, sample, _ptr(out)))
+        return out
+
+    def set_spins(self, sample: int, slot: int, s) -> None:
+        if hasattr(s, "data_ptr"):
+            assert s.is_contiguous() and s.numel() == self.N(sample) * 3
+        else:
+            s = np.ascontiguousarray(s, dtype=np.float32)
+            assert s.size == self.N(sample) * 3
+        _check(self._lib.hsg_set_spins(self._h, sample, slot, _ptr(s)))
+
+    def get_spins(self, sample: int, slot: int, out=None):
+        if out is None:
+            out = np.empty((self.N(sample), 3), dtype=np.float32)
+        _check(self._lib.hsg_get_spins(self._h, sample, slot, _ptr(out)))
+        return out
+
+    # -- Monte Carlo -----------------------------------------------------
+    def sweep_hb(self, n: int = 1) -> None:
+        _check(self._lib.hsg_sweep_hb(self._h, n))
+
+    def sweep_or(self, n: int = 1) -> None:
+        _check(self._lib.hsg_sweep_or(self._h, n))
+
+    def energy(self) -> None:
+        _check(self._lib.hsg_energy(self._h))
+
+    def get_energies(self) -> np.ndarray:
+        out = np.empty((self.S, self.R), dtype=np.float64)
+        _check(self._lib.hsg_get_energies(self._h, _ptr(out)))
+        return out
+
+    def set_energies(self, E) -> None:
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        assert E.size == self.S * self.R
+        _check(self._lib.hsg_set_energies(self._h, _ptr(E)))
+
+    def pt_swap(self) -> None:
+        _check(self._lib.hsg_pt_swap(self._h))
+
+    def get_perm(self) -> np.ndarray:
+        out = np.empty((self.S, self.n_replicas, self.NT), dtype=np.int32)
+        _check(self._lib.hsg_get_perm(self._h, _ptr(out)))
+        return out
+
+    def set_perm(self, perm) -> None:
+        perm = np.ascontiguousarray(perm, dtype=np.int32)
+        assert perm.size == self.S * self.n_replicas * self.NT
+        _check(self._lib.hsg_set_perm(self._h, _ptr(perm)))
+
+    def get_pt_accepts(self) -> np.ndarray:
+        out = np.empty((self.S, self.n_replicas, max(self.NT - 1, 1)), dtype=np.int64)
+        _check(self._lib.hsg_get_pt_accepts(self._h, _ptr(out)))
+        return out
+
+    def measure(self) -> None:
+        _check(self._lib.hsg_measure(self._h))
+
+    def run_steps(self, n: int) -> None:
+        _check(self._lib.hsg_run_steps(self._h, n))
+
+    def read_observables(self):
+        obs = np.empty((self.S, self.NT, NOBS), dtype=np.float64)
+        counts = np.empty((self.S, self.NT), dtype=np.int64)
+        _check(self._lib.hsg_read_observables(self._h, _ptr(obs), _ptr(counts)))
+        return obs, counts
+
+    def reset_observables(self) -> None:
+        _check(self._lib.hsg_reset_observables(self._h))
+
+    def get_counters(self) -> np.ndarray:
+        out = np.zeros(3, dtype=np.uint64)
+        _check(self._lib.hsg_get_counters(self._h, _ptr(out)))
+        return out
+
+    def set_counters(self, hb: int, pt: int, steps: int) -> None:
+        a = np.array([hb, pt, steps], dtype=np.uint64)
+        _check(self._lib.hsg_set_counters(self._h, _ptr(a)))
+
+    def get_launch_count(self) -> int:
+        out = np.zeros(1, dtype=np.uint64)
+        _check(self._lib.hsg_get_launch_count(self._h, _ptr(out)))
+        return int(out[0])
+
+    def save(self, path: str) -> None:
+        _check(self._lib.hsg_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        _check(self._lib.hsg_load(self._h, os.fsencode(path)))
+
+    def synchronize(self) -> None:
+        _check(self._lib.hsg_synchronize(self._h))

@@ -1,0 +1,836 @@
+// libhsg: host side of the C ABI declared in include/hsg.h.
+//
+// Owns every device buffer, validates arguments before touching state,
+// enqueues the kernels of kernels.cuh on the context's stream and replays one
+// Monte Carlo step (Sec. III, App. A.1) from captured CUDA graphs.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hsg.h"
+#include "kernels.cuh"
+
+using namespace hsg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hsg_status fail(hsg_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define HSG_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(HSG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+struct Bucket {
+  int L = 0, N = 0, S_b = 0, G = 0;
+  std::vector<int> samples;   // global sample ids, in order
+  int* d_samples = nullptr;
+  float* d_spins = nullptr;   // [S_b][G][3][N][V]
+  void* d_J = nullptr;        // f32 [S_b][3][N][6] or f16 [S_b][3][N][8]
+  int sweep_chunks = 0;       // blocks per lattice group in a half-sweep
+  double* d_epart = nullptr;  // [S_b*R][sweep_chunks]
+  int m_chunks = 0, P = 0;
+  double* d_mpart = nullptr;  // [S_b][NT][P][m_chunks][kNQ]
+  float* d_phase = nullptr;   // [L][2]
+};
+
+}  // namespace
+
+struct hsg_ctx {
+  int S = 0, n_rep = 0, NT = 0, R = 0, V = 1, prec = HSG_F32, layout = 0, n_or = 0;
+  int measure_every = 0;
+  uint64_t seed = 0;
+  std::vector<int> Ls;
+  std::vector<double> beta;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<Bucket> buckets;
+  std::vector<int> sample_bucket, sample_local;
+  int* d_perm = nullptr;        // [S][n_rep][NT] temperature -> slot
+  int* d_temp_of = nullptr;     // [S][R] slot -> temperature
+  double* d_beta = nullptr;     // [NT]
+  float* d_beta_f = nullptr;    // [NT]
+  double* d_E = nullptr;        // [S][R]
+  double* d_obs = nullptr;      // [S][NT][HSG_NOBS]
+  long long* d_counts = nullptr;  // [S][NT]
+  long long* d_pt_acc = nullptr;  // [S][n_rep][max(NT-1,1)]
+  uint32_t* d_counters = nullptr; // [0] HB sweeps, [1] PT sweeps
+  float* d_stage = nullptr;     // staging for spins [max N][3]
+  uint32_t* d_tmp_u32 = nullptr;
+  bool energy_valid = false;
+  uint64_t counters[3] = {0, 0, 0};
+  cudaGraphExec_t g_step = nullptr, g_step_m = nullptr;
+  uint64_t g_step_launches = 0, g_step_m_launches = 0;  // kernels per graph replay
+  uint64_t launches = 0;       // kernels enqueued by this context so far
+  uint64_t* launch_sink = nullptr;  // where enqueue helpers count launches
+};
+
+namespace {
+
+uint2 philox_key(uint64_t seed) {
+  return make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+size_t bond_elems(int prec) { return prec == HSG_F16 ? 8 : 6; }
+size_t bond_bytes(int prec) { return prec == HSG_F16 ? 16 : 24; }
+
+void free_ctx(hsg_ctx* h) {
+  if (!h) return;
+  if (h->g_step) cudaGraphExecDestroy(h->g_step);
+  if (h->g_step_m) cudaGraphExecDestroy(h->g_step_m);
+  for (Bucket& b : h->buckets) {
+    cudaFree(b.d_samples);
+    cudaFree(b.d_spins);
+    cudaFree(b.d_J);
+    cudaFree(b.d_epart);
+    cudaFree(b.d_mpart);
+    cudaFree(b.d_phase);
+  }
+  cudaFree(h->d_perm);
+  cudaFree(h->d_temp_of);
+  cudaFree(h->d_beta);
+  cudaFree(h->d_beta_f);
+  cudaFree(h->d_E);
+  cudaFree(h->d_obs);
+  cudaFree(h->d_counts);
+  cudaFree(h->d_pt_acc);
+  cudaFree(h->d_counters);
+  cudaFree(h->d_stage);
+  cudaFree(h->d_tmp_u32);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+template <typename T>
+hsg_status dalloc(T** p, size_t n) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(HSG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return HSG_OK;
+}
+
+#define HSG_TRY(expr)                  \
+  do {                                 \
+    hsg_status st_ = (expr);           \
+    if (st_ != HSG_OK) return st_;     \
+  } while (0)
+
+int acc_stride(const hsg_ctx* h) { return h->NT > 1 ? h->NT - 1 : 1; }
+
+// ----------------------------------------------------------------------------
+// Enqueue helpers (stream-ordered; used directly and under graph capture)
+// ----------------------------------------------------------------------------
+BucketView view(const Bucket& b) {
+  BucketView v;
+  v.spins = b.d_spins;
+  v.J = b.d_J;
+  v.sample_ids = b.d_samples;
+  v.L = b.L;
+  v.N = b.N;
+  v.S_b = b.S_b;
+  v.G = b.G;
+  return v;
+}
+
+template <int KIND>
+hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cudaStream_t st) {
+  SweepParams p;
+  p.b = view(b);
+  p.colour = colour;
+  p.chunks = b.sweep_chunks;
+  p.R = h->R;
+  p.temp_of = h->d_temp_of;
+  p.beta_f = h->d_beta_f;
+  p.key = philox_key(h->seed);
+  p.counters = h->d_counters;
+  p.e_partial = energy ? b.d_epart : nullptr;
+  const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.sweep_chunks);
+  *h->launch_sink += 1;
+  if (h->V == 2) {
+    if (h->prec == HSG_F16) k_sweep_half<KIND, 2, kPrecF16><<<grid, kSweepThreads, 0, st>>>(p);
+    else k_sweep_half<KIND, 2, kPrecF32><<<grid, kSweepThreads, 0, st>>>(p);
+  } else {
+    if (h->prec == HSG_F16) k_sweep_half<KIND, 1, kPrecF16><<<grid, kSweepThreads, 0, st>>>(p);
+    else k_sweep_half<KIND, 1, kPrecF32><<<grid, kSweepThreads, 0, st>>>(p);
+  }
+  HSG_CUDA(cudaGetLastError());
+  return HSG_OK;
+}
+
+hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st) {
+  *h->launch_sink += 1;
+  k_bump_counters<<<1, 1, 0, st>>>(h->d_counters, dhb, dpt);
+  HSG_CUDA(cudaGetLastError());
+  return HSG_OK;
+}
+
+hsg_status enqueue_hb_sweep(hsg_ctx* h, cudaStream_t st) {
+  for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kHB>(h, b, 0, false, st));
+  for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kHB>(h, b, 1, false, st));
+  return HSG_OK;
+}
+
+hsg_status enqueue_energy_finalize(hsg_ctx* h, cudaStream_t st) {
+  for (const Bucket& b : h->buckets) {
+    const int n_lat = b.S_b * h->R;
+    const int threads = 256;
+    const int blocks = (n_lat * 32 + threads - 1) / threads;
+    *h->launch_sink += 1;
+    k_energy_finalize<<<blocks, threads, 0, st>>>(b.d_epart, b.sweep_chunks, n_lat, b.d_samples, h->R, h->d_E);
+    HSG_CUDA(cudaGetLastError());
+  }
+  return HSG_OK;
+}
+
+// n overrelaxation sweeps; the white half of the last one writes energies.
+hsg_status enqueue_or_sweeps(hsg_ctx* h, int n, cudaStream_t st) {
+  for (int s = 0; s < n; ++s) {
+    const bool last = (s == n - 1);
+    for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kOR>(h, b, 0, false, st));
+    for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kOR>(h, b, 1, last, st));
+  }
+  if (n > 0) HSG_TRY(enqueue_energy_finalize(h, st));
+  return HSG_OK;
+}
+
+hsg_status enqueue_energy(hsg_ctx* h, cudaStream_t st) {
+  for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kEnergyOnly>(h, b, 1, true, st));
+  return enqueue_energy_finalize(h, st);
+}
+
+hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st) {
+  const int n_sets = h->S * h->n_rep;
+  const int threads = 128;
+  *h->launch_sink += 1;
+  k_pt_sweep<<<(n_sets + threads - 1) / threads, threads, 0, st>>>(
+      n_sets, h->n_rep, h->NT, h->R, h->d_beta, h->d_E, h->d_perm, h->d_temp_of, h->d_pt_acc,
+      philox_key(h->seed), h->d_counters);
+  HSG_CUDA(cudaGetLastError());
+  return HSG_OK;
+}
+
+hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
+  for (const Bucket& b : h->buckets) {
+    MeasureParams p;
+    p.b = view(b);
+    p.R = h->R;
+    p.n_rep = h->n_rep;
+    p.NT = h->NT;
+    p.P = b.P;
+    p.chunks = b.m_chunks;
+    p.perm = h->d_perm;
+    p.beta = h->d_beta;
+    p.phase = b.d_phase;
+    p.partial = b.d_mpart;
+    const unsigned grid = static_cast<unsigned>(b.S_b * h->NT * b.P * b.m_chunks);
+    const size_t smem = 2 * sizeof(float) * b.L;
+    *h->launch_sink += 2;
+    if (h->V == 2) {
+      if (h->prec == HSG_F16) k_measure<2, kPrecF16><<<grid, kMeasureThreads, smem, st>>>(p);
+      else k_measure<2, kPrecF32><<<grid, kMeasureThreads, smem, st>>>(p);
+    } else {
+      if (h->prec == HSG_F16) k_measure<1, kPrecF16><<<grid, kMeasureThreads, smem, st>>>(p);
+      else k_measure<1, kPrecF32><<<grid, kMeasureThreads, smem, st>>>(p);
+    }
+    HSG_CUDA(cudaGetLastError());
+    const int units = b.S_b * h->NT;
+    k_measure_finalize<<<(units + 127) / 128, 128, 0, st>>>(b.d_mpart, b.d_samples, b.S_b, h->NT, b.P, b.m_chunks,
+                                                           h->n_rep, h->R, b.N, h->d_perm, h->d_E, h->d_obs,
+                                                           h->d_counts);
+    HSG_CUDA(cudaGetLastError());
+  }
+  return HSG_OK;
+}
+
+// One Monte Carlo step: HB sweep, n_or OR sweeps (energies fused into the
+// last), energies, PT, optional measurement, counters.
+hsg_status enqueue_step(hsg_ctx* h, bool with_measure, cudaStream_t st) {
+  HSG_TRY(enqueue_hb_sweep(h, st));
+  if (h->n_or > 0) HSG_TRY(enqueue_or_sweeps(h, h->n_or, st));
+  else HSG_TRY(enqueue_energy(h, st));
+  if (h->NT > 1) HSG_TRY(enqueue_pt(h, st));
+  if (with_measure) HSG_TRY(enqueue_measure(h, st));
+  return enqueue_bump(h, 1, 1, st);
+}
+
+hsg_status capture_graph(hsg_ctx* h, bool with_measure, cudaGraphExec_t* out, uint64_t* n_kernels) {
+  cudaGraph_t graph = nullptr;
+  HSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  *n_kernels = 0;
+  h->launch_sink = n_kernels;
+  hsg_status st = enqueue_step(h, with_measure, h->cap_stream);
+  h->launch_sink = &h->launches;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (st != HSG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(HSG_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(HSG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return HSG_OK;
+}
+
+hsg_status check_sample(const hsg_ctx* h, int sample) {
+  if (sample < 0 || sample >= h->S) return fail(HSG_EINVAL, "sample index out of range");
+  return HSG_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* hsg_last_error(void) { return g_last_error.c_str(); }
+
+int hsg_version(void) { return HSG_VERSION; }
+
+hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
+  if (!out) return fail(HSG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(HSG_EINVAL, "cfg is NULL");
+  if (cfg->n_samples < 1 || !cfg->L) return fail(HSG_EINVAL, "n_samples must be >= 1 and L non-NULL");
+  if (cfg->n_replicas < 1 || cfg->n_temps < 1 || !cfg->beta)
+    return fail(HSG_EINVAL, "n_replicas and n_temps must be >= 1 and beta non-NULL");
+  if (cfg->coupling_prec != HSG_F32 && cfg->coupling_prec != HSG_F16)
+    return fail(HSG_EINVAL, "coupling_prec must be HSG_F32 or HSG_F16");
+  if (cfg->layout != HSG_LAYOUT_PLAIN && cfg->layout != HSG_LAYOUT_BATCHED)
+    return fail(HSG_EINVAL, "layout must be HSG_LAYOUT_PLAIN or HSG_LAYOUT_BATCHED");
+  if (cfg->n_or < 0 || cfg->measure_every < 0) return fail(HSG_EINVAL, "n_or and measure_every must be >= 0");
+  for (int s = 0; s < cfg->n_samples; ++s) {
+    const int L = cfg->L[s];
+    if (L < 4 || L > 512 || (L & 1)) return fail(HSG_EINVAL, "each L must be even and in [4, 512]");
+  }
+  for (int k = 0; k < cfg->n_temps; ++k) {
+    if (!(cfg->beta[k] >= 0.0) || !(cfg->beta[k] < 1e300))
+      return fail(HSG_EINVAL, "beta must be finite and >= 0");
+    if (k > 0 && !(cfg->beta[k] > cfg->beta[k - 1])) return fail(HSG_EINVAL, "beta must be strictly increasing");
+  }
+  const long long R = static_cast<long long>(cfg->n_replicas) * cfg->n_temps;
+  const int V = cfg->layout == HSG_LAYOUT_BATCHED ? 2 : 1;
+  if (R % V != 0) return fail(HSG_EINVAL, "the batched layout needs an even number of lattices per sample");
+  if (R * cfg->n_samples > 0x7fffffffLL) return fail(HSG_EINVAL, "too many lattices");
+
+  hsg_ctx* h = new (std::nothrow) hsg_ctx();
+  if (!h) return fail(HSG_ENOMEM, "host allocation failed");
+  h->S = cfg->n_samples;
+  h->n_rep = cfg->n_replicas;
+  h->NT = cfg->n_temps;
+  h->R = static_cast<int>(R);
+  h->V = V;
+  h->prec = cfg->coupling_prec;
+  h->layout = cfg->layout;
+  h->n_or = cfg->n_or;
+  h->measure_every = cfg->measure_every;
+  h->seed = cfg->seed;
+  h->stream = static_cast<cudaStream_t>(cfg->stream);
+  h->launch_sink = &h->launches;
+  h->Ls.assign(cfg->L, cfg->L + cfg->n_samples);
+  h->beta.assign(cfg->beta, cfg->beta + cfg->n_temps);
+
+  auto bail = [&](hsg_status st) {
+    std::string msg = g_last_error;
+    free_ctx(h);
+    g_last_error = msg;
+    return st;
+  };
+
+  // Buckets: samples grouped by L, in order of first appearance.
+  h->sample_bucket.assign(h->S, -1);
+  h->sample_local.assign(h->S, -1);
+  for (int s = 0; s < h->S; ++s) {
+    int bi = -1;
+    for (size_t j = 0; j < h->buckets.size(); ++j)
+      if (h->buckets[j].L == h->Ls[s]) bi = static_cast<int>(j);
+    if (bi < 0) {
+      h->buckets.emplace_back();
+      bi = static_cast<int>(h->buckets.size()) - 1;
+      h->buckets[bi].L = h->Ls[s];
+    }
+    h->sample_bucket[s] = bi;
+    h->sample_local[s] = static_cast<int>(h->buckets[bi].samples.size());
+    h->buckets[bi].samples.push_back(s);
+  }
+
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    fail(HSG_ECUDA, "cudaStreamCreate failed");
+    return bail(HSG_ECUDA);
+  }
+
+  size_t max_N = 0;
+  for (Bucket& b : h->buckets) {
+    b.N = b.L * b.L * b.L;
+    b.S_b = static_cast<int>(b.samples.size());
+    b.G = h->R / V;
+    b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
+    b.P = (h->n_rep + 1) / 2;
+    const int units = b.S_b * h->NT * b.P;
+    const int by_size = std::max(1, b.N / (kMeasureThreads * 16));
+    const int by_fill = std::max(1, (2 * 148 + units - 1) / units);
+    b.m_chunks = std::max(1, std::min(by_size, by_fill));
+    max_N = std::max<size_t>(max_N, b.N);
+    const size_t n_spin = static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
+    hsg_status st;
+    if ((st = dalloc(&b.d_samples, b.S_b)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_spins, n_spin)) != HSG_OK) return bail(st);
+    const size_t jbytes = static_cast<size_t>(b.S_b) * 3 * b.N * bond_bytes(h->prec);
+    if ((st = dalloc(reinterpret_cast<char**>(&b.d_J), jbytes)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_epart, static_cast<size_t>(b.S_b) * h->R * b.sweep_chunks)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_mpart, static_cast<size_t>(units) * b.m_chunks * kNQ)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_phase, 2 * static_cast<size_t>(b.L))) != HSG_OK) return bail(st);
+    if (cudaMemcpy(b.d_samples, b.samples.data(), sizeof(int) * b.S_b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b.d_J, 0, jbytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(HSG_ECUDA, "initialising bucket buffers failed");
+      return bail(HSG_ECUDA);
+    }
+    std::vector<float> ph(2 * b.L);
+    for (int x = 0; x < b.L; ++x) {
+      const double a = 2.0 * 3.14159265358979323846 * x / b.L;
+      ph[2 * x] = static_cast<float>(std::cos(a));
+      ph[2 * x + 1] = static_cast<float>(std::sin(a));
+    }
+    if (cudaMemcpy(b.d_phase, ph.data(), sizeof(float) * 2 * b.L, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      fail(HSG_ECUDA, "phase table upload failed");
+      return bail(HSG_ECUDA);
+    }
+    const size_t per_block = static_cast<size_t>(b.N) * V;
+    k_fill_spins<<<static_cast<unsigned>((n_spin + 255) / 256), 256>>>(b.d_spins, per_block, n_spin);
+  }
+
+  const size_t S = h->S, NT = h->NT;
+  hsg_status st;
+  if ((st = dalloc(&h->d_perm, S * h->n_rep * NT)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_temp_of, S * h->R)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_beta, NT)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_beta_f, NT)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_E, S * h->R)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_obs, S * NT * HSG_NOBS)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_counts, S * NT)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_pt_acc, S * h->n_rep * acc_stride(h))) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_counters, 2)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_stage, 3 * max_N)) != HSG_OK) return bail(st);
+
+  std::vector<int> perm(S * h->n_rep * NT), temp_of(S * h->R);
+  for (size_t s = 0; s < S; ++s)
+    for (int r = 0; r < h->n_rep; ++r)
+      for (size_t k = 0; k < NT; ++k) {
+        const int slot = r * static_cast<int>(NT) + static_cast<int>(k);
+        perm[(s * h->n_rep + r) * NT + k] = slot;
+        temp_of[s * h->R + slot] = static_cast<int>(k);
+      }
+  std::vector<float> bf(NT);
+  for (size_t k = 0; k < NT; ++k) bf[k] = static_cast<float>(h->beta[k]);
+  if (cudaMemcpy(h->d_perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_temp_of, temp_of.data(), sizeof(int) * temp_of.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_beta, h->beta.data(), sizeof(double) * NT, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_beta_f, bf.data(), sizeof(float) * NT, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(h->d_E, 0, sizeof(double) * S * h->R) != cudaSuccess ||
+      cudaMemset(h->d_obs, 0, sizeof(double) * S * NT * HSG_NOBS) != cudaSuccess ||
+      cudaMemset(h->d_counts, 0, sizeof(long long) * S * NT) != cudaSuccess ||
+      cudaMemset(h->d_pt_acc, 0, sizeof(long long) * S * h->n_rep * acc_stride(h)) != cudaSuccess ||
+      cudaMemset(h->d_counters, 0, sizeof(uint32_t) * 2) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    fail(HSG_ECUDA, std::string("initialising context buffers failed: ") + cudaGetErrorString(e));
+    return bail(HSG_ECUDA);
+  }
+  *out = h;
+  return HSG_OK;
+}
+
+void hsg_destroy(hsg_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_ctx(h);
+}
+
+hsg_status hsg_synchronize(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
+  if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  const size_t N = b.N;
+  const size_t per_sample = 3 * N * bond_elems(h->prec);
+  std::vector<char> buf(3 * N * bond_bytes(h->prec));
+  if (h->prec == HSG_F32) {
+    float* out = reinterpret_cast<float*>(buf.data());
+    for (size_t i = 0; i < N; ++i)
+      for (int mu = 0; mu < 3; ++mu)
+        for (int e = 0; e < 6; ++e) out[(mu * N + i) * 6 + e] = J6[(i * 3 + mu) * 6 + e];
+  } else {
+    __half* out = reinterpret_cast<__half*>(buf.data());
+    for (size_t i = 0; i < N; ++i)
+      for (int mu = 0; mu < 3; ++mu) {
+        for (int e = 0; e < 6; ++e) out[(mu * N + i) * 8 + e] = __float2half_rn(J6[(i * 3 + mu) * 6 + e]);
+        out[(mu * N + i) * 8 + 6] = __float2half_rn(0.0f);
+        out[(mu * N + i) * 8 + 7] = __float2half_rn(0.0f);
+      }
+  }
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  char* dst = static_cast<char*>(b.d_J) + sb * per_sample * (h->prec == HSG_F16 ? 2 : 4);
+  HSG_CUDA(cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_couplings(hsg_t h, int sample, float* J6) {
+  if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  const size_t N = b.N;
+  const size_t per_sample = 3 * N * bond_elems(h->prec);
+  std::vector<char> buf(3 * N * bond_bytes(h->prec));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  const char* src = static_cast<const char*>(b.d_J) + sb * per_sample * (h->prec == HSG_F16 ? 2 : 4);
+  HSG_CUDA(cudaMemcpy(buf.data(), src, buf.size(), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i)
+    for (int mu = 0; mu < 3; ++mu)
+      for (int e = 0; e < 6; ++e) {
+        float v;
+        if (h->prec == HSG_F32) v = reinterpret_cast<const float*>(buf.data())[(mu * N + i) * 6 + e];
+        else v = __half2float(reinterpret_cast<const __half*>(buf.data())[(mu * N + i) * 8 + e]);
+        J6[(i * 3 + mu) * 6 + e] = v;
+      }
+  return HSG_OK;
+}
+
+static hsg_status spin_slot_args(hsg_t h, int sample, int slot) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  HSG_TRY(check_sample(h, sample));
+  if (slot < 0 || slot >= h->R) return fail(HSG_EINVAL, "slot out of range");
+  return HSG_OK;
+}
+
+hsg_status hsg_set_spins(hsg_t h, int sample, int slot, const float* s) {
+  HSG_TRY(spin_slot_args(h, sample, slot));
+  if (!s) return fail(HSG_EINVAL, "spins pointer is NULL");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  float* base = b.d_spins + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  HSG_CUDA(cudaMemcpyAsync(h->d_stage, s, sizeof(float) * 3 * b.N, cudaMemcpyHostToDevice, h->stream));
+  k_scatter_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(h->d_stage, base, b.N, h->V, slot % h->V);
+  HSG_CUDA(cudaGetLastError());
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float* s_out) {
+  HSG_TRY(spin_slot_args(h, sample, slot));
+  if (!s_out) return fail(HSG_EINVAL, "output pointer is NULL");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  const float* base = b.d_spins + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  k_gather_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(base, h->d_stage, b.N, h->V, slot % h->V);
+  HSG_CUDA(cudaGetLastError());
+  HSG_CUDA(cudaMemcpyAsync(s_out, h->d_stage, sizeof(float) * 3 * b.N, cudaMemcpyDeviceToHost, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_sweep_hb(hsg_t h, int n) {
+  if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
+  for (int s = 0; s < n; ++s) {
+    HSG_TRY(enqueue_hb_sweep(h, h->stream));
+    HSG_TRY(enqueue_bump(h, 1, 0, h->stream));
+    h->counters[0] += 1;
+  }
+  if (n > 0) h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_sweep_or(hsg_t h, int n) {
+  if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
+  if (n == 0) return HSG_OK;
+  HSG_TRY(enqueue_or_sweeps(h, n, h->stream));
+  h->energy_valid = true;
+  return HSG_OK;
+}
+
+hsg_status hsg_energy(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  HSG_TRY(enqueue_energy(h, h->stream));
+  h->energy_valid = true;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_energies(hsg_t h, double* E_out) {
+  if (!h || !E_out) return fail(HSG_EINVAL, "NULL argument");
+  if (!h->energy_valid) HSG_TRY(hsg_energy(h));
+  HSG_CUDA(cudaMemcpyAsync(E_out, h->d_E, sizeof(double) * h->S * h->R, cudaMemcpyDeviceToHost, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_set_energies(hsg_t h, const double* E) {
+  if (!h || !E) return fail(HSG_EINVAL, "NULL argument");
+  HSG_CUDA(cudaMemcpyAsync(h->d_E, E, sizeof(double) * h->S * h->R, cudaMemcpyHostToDevice, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  h->energy_valid = true;
+  return HSG_OK;
+}
+
+hsg_status hsg_pt_swap(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  if (!h->energy_valid) HSG_TRY(hsg_energy(h));
+  if (h->NT > 1) HSG_TRY(enqueue_pt(h, h->stream));
+  HSG_TRY(enqueue_bump(h, 0, 1, h->stream));
+  h->counters[1] += 1;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_perm(hsg_t h, int* perm_out) {
+  if (!h || !perm_out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_CUDA(cudaMemcpyAsync(perm_out, h->d_perm, sizeof(int) * h->S * h->n_rep * h->NT, cudaMemcpyDeviceToHost,
+                           h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_set_perm(hsg_t h, const int* perm) {
+  if (!h || !perm) return fail(HSG_EINVAL, "NULL argument");
+  const int NT = h->NT;
+  std::vector<int> temp_of(static_cast<size_t>(h->S) * h->R);
+  for (int s = 0; s < h->S; ++s)
+    for (int r = 0; r < h->n_rep; ++r) {
+      std::vector<char> seen(NT, 0);
+      for (int k = 0; k < NT; ++k) {
+        const int slot = perm[(static_cast<size_t>(s) * h->n_rep + r) * NT + k];
+        if (slot < r * NT || slot >= (r + 1) * NT || seen[slot - r * NT])
+          return fail(HSG_EINVAL, "perm must map each replica's temperatures onto that replica's slots");
+        seen[slot - r * NT] = 1;
+        temp_of[static_cast<size_t>(s) * h->R + slot] = k;
+      }
+    }
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_CUDA(cudaMemcpy(h->d_perm, perm, sizeof(int) * h->S * h->n_rep * NT, cudaMemcpyHostToDevice));
+  HSG_CUDA(cudaMemcpy(h->d_temp_of, temp_of.data(), sizeof(int) * temp_of.size(), cudaMemcpyHostToDevice));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_pt_accepts(hsg_t h, long long* acc_out) {
+  if (!h || !acc_out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_CUDA(cudaMemcpyAsync(acc_out, h->d_pt_acc, sizeof(long long) * h->S * h->n_rep * acc_stride(h),
+                           cudaMemcpyDeviceToHost, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_measure(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  if (!h->energy_valid) HSG_TRY(hsg_energy(h));
+  return enqueue_measure(h, h->stream);
+}
+
+hsg_status hsg_run_steps(hsg_t h, int n_steps) {
+  if (!h || n_steps < 0) return fail(HSG_EINVAL, "bad handle or n_steps < 0");
+  if (n_steps == 0) return HSG_OK;
+  if (!h->g_step) HSG_TRY(capture_graph(h, false, &h->g_step, &h->g_step_launches));
+  if (h->measure_every > 0 && !h->g_step_m) HSG_TRY(capture_graph(h, true, &h->g_step_m, &h->g_step_m_launches));
+  for (int s = 0; s < n_steps; ++s) {
+    const uint64_t next = h->counters[2] + 1;
+    const bool m = h->measure_every > 0 && (next % static_cast<uint64_t>(h->measure_every)) == 0;
+    HSG_CUDA(cudaGraphLaunch(m ? h->g_step_m : h->g_step, h->stream));
+    h->launches += m ? h->g_step_m_launches : h->g_step_launches;
+    h->counters[0] += 1;
+    h->counters[1] += 1;
+    h->counters[2] = next;
+  }
+  h->energy_valid = true;
+  return HSG_OK;
+}
+
+hsg_status hsg_read_observables(hsg_t h, double* obs_out, long long* counts_out) {
+  if (!h || !obs_out) return fail(HSG_EINVAL, "NULL argument");
+  const size_t n = static_cast<size_t>(h->S) * h->NT;
+  HSG_CUDA(cudaMemcpyAsync(obs_out, h->d_obs, sizeof(double) * n * HSG_NOBS, cudaMemcpyDeviceToHost, h->stream));
+  if (counts_out)
+    HSG_CUDA(cudaMemcpyAsync(counts_out, h->d_counts, sizeof(long long) * n, cudaMemcpyDeviceToHost, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_reset_observables(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  const size_t n = static_cast<size_t>(h->S) * h->NT;
+  HSG_CUDA(cudaMemsetAsync(h->d_obs, 0, sizeof(double) * n * HSG_NOBS, h->stream));
+  HSG_CUDA(cudaMemsetAsync(h->d_counts, 0, sizeof(long long) * n, h->stream));
+  HSG_CUDA(cudaMemsetAsync(h->d_pt_acc, 0, sizeof(long long) * h->S * h->n_rep * acc_stride(h), h->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_counters(hsg_t h, uint64_t out[3]) {
+  if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
+  for (int j = 0; j < 3; ++j) out[j] = h->counters[j];
+  return HSG_OK;
+}
+
+hsg_status hsg_get_launch_count(hsg_t h, uint64_t* out) {
+  if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
+  *out = h->launches;
+  return HSG_OK;
+}
+
+hsg_status hsg_set_counters(hsg_t h, const uint64_t in[3]) {
+  if (!h || !in) return fail(HSG_EINVAL, "NULL argument");
+  const uint32_t dev[2] = {static_cast<uint32_t>(in[0]), static_cast<uint32_t>(in[1])};
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_CUDA(cudaMemcpy(h->d_counters, dev, sizeof(dev), cudaMemcpyHostToDevice));
+  for (int j = 0; j < 3; ++j) h->counters[j] = in[j];
+  return HSG_OK;
+}
+
+// Checkpoint format: magic, version, a fingerprint of the configuration,
+// host counters, then each device array in a fixed order.
+static const uint64_t kMagic = 0x31475348u;  // "HSG1"
+
+static void fingerprint(const hsg_ctx* h, std::vector<int64_t>& f) {
+  f.clear();
+  f.push_back(h->S);
+  f.push_back(h->n_rep);
+  f.push_back(h->NT);
+  f.push_back(h->V);
+  f.push_back(h->prec);
+  for (int L : h->Ls) f.push_back(L);
+}
+
+namespace {
+struct DevArray {
+  void* ptr;
+  size_t bytes;
+};
+std::vector<DevArray> checkpoint_arrays(hsg_ctx* h) {
+  std::vector<DevArray> a;
+  for (Bucket& b : h->buckets) {
+    a.push_back({b.d_spins, sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N});
+    a.push_back({b.d_J, static_cast<size_t>(b.S_b) * 3 * b.N * bond_bytes(h->prec)});
+  }
+  const size_t S = h->S, NT = h->NT;
+  a.push_back({h->d_perm, sizeof(int) * S * h->n_rep * NT});
+  a.push_back({h->d_temp_of, sizeof(int) * S * h->R});
+  a.push_back({h->d_E, sizeof(double) * S * h->R});
+  a.push_back({h->d_obs, sizeof(double) * S * NT * HSG_NOBS});
+  a.push_back({h->d_counts, sizeof(long long) * S * NT});
+  a.push_back({h->d_pt_acc, sizeof(long long) * S * h->n_rep * acc_stride(h)});
+  a.push_back({h->d_counters, sizeof(uint32_t) * 2});
+  return a;
+}
+}  // namespace
+
+hsg_status hsg_save(hsg_t h, const char* path) {
+  if (!h || !path) return fail(HSG_EINVAL, "NULL argument");
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(HSG_EIO, std::string("cannot open ") + path);
+  std::vector<int64_t> fp;
+  fingerprint(h, fp);
+  const uint64_t hdr[3] = {kMagic, HSG_VERSION, fp.size()};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(fp.data(), sizeof(int64_t), fp.size(), f) == fp.size() &&
+            std::fwrite(h->counters, sizeof(h->counters), 1, f) == 1;
+  const int ev = h->energy_valid ? 1 : 0;
+  ok = ok && std::fwrite(&ev, sizeof(ev), 1, f) == 1;
+  for (const DevArray& d : checkpoint_arrays(h)) {
+    if (!ok) break;
+    std::vector<char> buf(d.bytes);
+    if (cudaMemcpy(buf.data(), d.ptr, d.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      cudaGetLastError();
+      return fail(HSG_ECUDA, "device read during checkpoint failed");
+    }
+    ok = std::fwrite(buf.data(), 1, d.bytes, f) == d.bytes;
+  }
+  if (std::fclose(f) != 0) ok = false;
+  if (!ok) return fail(HSG_EIO, std::string("write failed: ") + path);
+  return HSG_OK;
+}
+
+hsg_status hsg_load(hsg_t h, const char* path) {
+  if (!h || !path) return fail(HSG_EINVAL, "NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(HSG_EIO, std::string("cannot open ") + path);
+  std::vector<int64_t> fp, fp_file;
+  fingerprint(h, fp);
+  uint64_t hdr[3];
+  uint64_t counters[3];
+  int ev = 0;
+  bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kMagic && hdr[1] == HSG_VERSION &&
+            hdr[2] == fp.size();
+  if (ok) {
+    fp_file.resize(fp.size());
+    ok = std::fread(fp_file.data(), sizeof(int64_t), fp.size(), f) == fp.size() && fp_file == fp;
+  }
+  if (!ok) {
+    std::fclose(f);
+    return fail(HSG_EINVAL, "checkpoint does not match this context's configuration");
+  }
+  ok = std::fread(counters, sizeof(counters), 1, f) == 1 && std::fread(&ev, sizeof(ev), 1, f) == 1;
+  std::vector<DevArray> arrays = checkpoint_arrays(h);
+  std::vector<std::vector<char>> bufs;
+  for (const DevArray& d : arrays) {
+    if (!ok) break;
+    bufs.emplace_back(d.bytes);
+    ok = std::fread(bufs.back().data(), 1, d.bytes, f) == d.bytes;
+  }
+  std::fclose(f);
+  if (!ok) return fail(HSG_EIO, std::string("truncated checkpoint: ") + path);
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  for (size_t j = 0; j < arrays.size(); ++j)
+    HSG_CUDA(cudaMemcpy(arrays[j].ptr, bufs[j].data(), arrays[j].bytes, cudaMemcpyHostToDevice));
+  for (int j = 0; j < 3; ++j) h->counters[j] = counters[j];
+  h->energy_valid = ev != 0;
+  return HSG_OK;
+}
+
+hsg_status hsg_philox4x32_10(const uint32_t* in, long n, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!in || !out))) return fail(HSG_EINVAL, "bad arguments");
+  if (n == 0) return HSG_OK;
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  HSG_TRY(dalloc(&d_in, 6 * static_cast<size_t>(n)));
+  if (dalloc(&d_out, 4 * static_cast<size_t>(n)) != HSG_OK) {
+    cudaFree(d_in);
+    return HSG_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d_in, in, sizeof(uint32_t) * 6 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_philox_eval<<<static_cast<unsigned>((n + 255) / 256), 256>>>(d_in, n, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return fail(HSG_ECUDA, std::string("philox evaluation failed: ") + cudaGetErrorString(e));
+  return HSG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,570 @@
+// Device kernels of libhsg: checkerboard heat-bath / overrelaxation sweeps with
+// the fused energy, parallel tempering and the overlap/chirality measurement.
+//
+// Device layout of one bucket (samples of equal L; N = L^3 sites, V lattices
+// interleaved per element, G = R/V lattice groups per sample):
+//   spins   float [S_b][G][3][N][V]   component planes, lattice lane innermost
+//   J f32   float [S_b][3][N][6]      bond (i, i+e_mu) at [mu][i]: xx,yy,zz,xy,xz,yz
+//   J f16   half  [S_b][3][N][8]      same six entries + two zero pads (16 B/bond)
+// Site i = x + L*(y + L*z); black sites have x+y+z even.
+#pragma once
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "philox.cuh"
+
+namespace hsg {
+
+enum : int { kHB = 0, kOR = 1, kEnergyOnly = 2 };
+enum : int { kPrecF32 = 0, kPrecF16 = 1 };
+constexpr int kSweepThreads = 256;
+constexpr int kMeasureThreads = 256;
+constexpr int kNQ = 30;  // raw measurement sums per pair, see k_measure
+
+struct BucketView {
+  float* spins;
+  const void* J;
+  const int* sample_ids;  // [S_b] global sample index
+  int L, N, S_b, G;
+};
+
+struct SweepParams {
+  BucketView b;
+  int colour;              // 0 black, 1 white
+  int chunks;              // blocks per lattice group
+  int R;                   // lattices per sample
+  const int* temp_of;      // [S][R] temperature index of each slot
+  const float* beta_f;     // [N_T]
+  uint2 key;               // Philox key
+  const uint32_t* counters;  // [0] heat-bath sweep counter, [1] PT counter
+  double* e_partial;       // [S_b*R][chunks] energy partials, or null
+};
+
+// ---------------------------------------------------------------------------
+// Loads
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ void load_bond(const void* J, size_t bond, float (&j)[6]) {
+  if constexpr (PREC == kPrecF32) {
+    const float2* p = reinterpret_cast<const float2*>(static_cast<const float*>(J) + bond * 6);
+    const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    j[0] = a.x; j[1] = a.y; j[2] = b.x; j[3] = b.y; j[4] = c.x; j[5] = c.y;
+  } else {
+    const uint4 u = __ldg(static_cast<const uint4*>(J) + bond);
+    __half2 h0, h1, h2;
+    *reinterpret_cast<uint32_t*>(&h0) = u.x;
+    *reinterpret_cast<uint32_t*>(&h1) = u.y;
+    *reinterpret_cast<uint32_t*>(&h2) = u.z;
+    const float2 a = __half22float2(h0), b = __half22float2(h1), c = __half22float2(h2);
+    j[0] = a.x; j[1] = a.y; j[2] = b.x; j[3] = b.y; j[4] = c.x; j[5] = c.y;
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void load_spin(const float* base, size_t plane, int i, float (&s)[3][V]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (V == 2) {
+      const float2 t = __ldg(reinterpret_cast<const float2*>(base + c * plane) + i);
+      s[c][0] = t.x;
+      s[c][1] = t.y;
+    } else {
+      s[c][0] = __ldg(base + c * plane + i);
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void store_spin(float* base, size_t plane, int i, const float (&s)[3][V]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (V == 2) {
+      reinterpret_cast<float2*>(base + c * plane)[i] = make_float2(s[c][0], s[c][1]);
+    } else {
+      base[c * plane + i] = s[c][0];
+    }
+  }
+}
+
+// h += J s for the symmetric J = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]].
+template <int V>
+__device__ __forceinline__ void add_bond(const float (&j)[6], const float (&s)[3][V], float (&h)[3][V]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    h[0][v] = fmaf(j[0], s[0][v], fmaf(j[3], s[1][v], fmaf(j[4], s[2][v], h[0][v])));
+    h[1][v] = fmaf(j[3], s[0][v], fmaf(j[1], s[1][v], fmaf(j[5], s[2][v], h[1][v])));
+    h[2][v] = fmaf(j[4], s[0][v], fmaf(j[5], s[1][v], fmaf(j[2], s[2][v], h[2][v])));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-spin updates (App. A.1)
+// ---------------------------------------------------------------------------
+// Heat-bath: s ~ exp(beta s.h) on the sphere.  u = cos(angle to h) by the
+// inverse CDF written for w = 1 - u (w = -log1p(r0 expm1(-2 kappa))/kappa,
+// kappa = beta|h|, continuous limit 2 r0 for kappa < 1e-30); azimuth 2 pi r1
+// in the orthonormal frame of Duff et al. (JCGT 6(1), 2017); axis e_z if h=0.
+__device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, float beta,
+                                               uint32_t w0, uint32_t w1,
+                                               float& sx, float& sy, float& sz) {
+  const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+  const float hn = sqrtf(hh);
+  const float kappa = beta * hn;
+  const float r0 = uniform23(w0);
+  const float r1 = uniform23(w1);
+  // w = -log(1 - y)/kappa with y = r0 (1 - e^{-2 kappa}).  In binary32 the
+  // single expression log1p(r0 expm1(-2 kappa)) loses all accuracy when y is
+  // close to 1 (expm1 rounds to -1 and 1 - y cancels), so the two regimes are
+  // evaluated separately: log1p(-y) for y < 1/2, and for y >= 1/2 the
+  // logarithm of 1 - y = (1 - r0) + r0 e^{-2 kappa}, a sum of two positive
+  // terms in which 1 - r0 is exact.
+  float w;
+  if (kappa < 1e-30f) {
+    w = 2.0f * r0;
+  } else {
+    const float y = -r0 * expm1f(-2.0f * kappa);
+    const float lg = (y < 0.5f) ? log1pf(-y) : logf(fmaf(r0, expf(-2.0f * kappa), 1.0f - r0));
+    w = -lg / kappa;
+  }
+  w = fminf(fmaxf(w, 0.0f), 2.0f);
+  const float u = 1.0f - w;
+  const float st = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
+  float sp, cp;
+  sincospif(2.0f * r1, &sp, &cp);
+  float nx = 0.0f, ny = 0.0f, nz = 1.0f;
+  if (hn > 0.0f) {
+    const float inv = 1.0f / hn;
+    nx = hx * inv;
+    ny = hy * inv;
+    nz = hz * inv;
+  }
+  const float sgn = copysignf(1.0f, nz);
+  const float p = -1.0f / (sgn + nz);
+  const float q = nx * ny * p;
+  const float e1x = fmaf(sgn * nx * nx, p, 1.0f), e1y = sgn * q, e1z = -sgn * nx;
+  const float e2x = q, e2y = fmaf(ny * ny, p, sgn), e2z = -ny;
+  const float ax = fmaf(cp, e1x, sp * e2x), ay = fmaf(cp, e1y, sp * e2y), az = fmaf(cp, e1z, sp * e2z);
+  sx = fmaf(u, nx, st * ax);
+  sy = fmaf(u, ny, st * ay);
+  sz = fmaf(u, nz, st * az);
+}
+
+// Overrelaxation: reflection of s about h, s' = 2h(h.s)/h^2 - s.
+__device__ __forceinline__ void overrelax(float hx, float hy, float hz, float& sx, float& sy, float& sz) {
+  const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+  if (hh > 0.0f) {
+    const float hs = fmaf(hx, sx, fmaf(hy, sy, hz * sz));
+    const float f = 2.0f * hs / hh;
+    sx = fmaf(f, hx, -sx);
+    sy = fmaf(f, hy, -sy);
+    sz = fmaf(f, hz, -sz);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// One colour half-sweep of every lattice of a bucket.  Thread = one site of
+// the colour x V lattices of one group; the six neighbours are of the other
+// colour and are only read.  With e_partial set, each block also writes
+// -sum s.h over its sites (per lattice) -- on the white half this is the
+// lattice energy, since every bond has exactly one white end and
+// overrelaxation keeps s.h.
+// ---------------------------------------------------------------------------
+template <int KIND, int V, int PREC>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
+  const BucketView& b = p.b;
+  const int gi = blockIdx.x / p.chunks;  // lattice group within the bucket
+  const int chunk = blockIdx.x - gi * p.chunks;
+  const int ic = chunk * kSweepThreads + threadIdx.x;
+  const int L = b.L, N = b.N, half = L >> 1;
+  const bool active = ic < (N >> 1);
+  const int sb = gi / b.G, g = gi - sb * b.G;
+  float e_acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) e_acc[v] = 0.0f;
+
+  if (active) {
+    const int row = ic / half;
+    const int k = ic - row * half;
+    const int y = row % L;
+    const int z = row / L;
+    const int x = 2 * k + ((p.colour + y + z) & 1);
+    const int i = x + L * row;
+    const int LL = L * L;
+    const int ixm = (x == 0) ? i + (L - 1) : i - 1;
+    const int ixp = (x == L - 1) ? i - (L - 1) : i + 1;
+    const int iym = (y == 0) ? i + (L - 1) * L : i - L;
+    const int iyp = (y == L - 1) ? i - (L - 1) * L : i + L;
+    const int izm = (z == 0) ? i + (L - 1) * LL : i - LL;
+    const int izp = (z == L - 1) ? i - (L - 1) * LL : i + LL;
+
+    float* base = b.spins + static_cast<size_t>(gi) * 3 * N * V;
+    const size_t plane = static_cast<size_t>(N) * V;
+    const size_t jb = static_cast<size_t>(sb) * 3 * N;
+
+    float h[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) h[c][v] = 0.0f;
+    float j[6];
+    float s[3][V];
+    load_bond<PREC>(b.J, jb + i, j);              load_spin<V>(base, plane, ixp, s); add_bond<V>(j, s, h);
+    load_bond<PREC>(b.J, jb + ixm, j);            load_spin<V>(base, plane, ixm, s); add_bond<V>(j, s, h);
+    load_bond<PREC>(b.J, jb + N + i, j);          load_spin<V>(base, plane, iyp, s); add_bond<V>(j, s, h);
+    load_bond<PREC>(b.J, jb + N + iym, j);        load_spin<V>(base, plane, iym, s); add_bond<V>(j, s, h);
+    load_bond<PREC>(b.J, jb + 2 * size_t(N) + i, j);   load_spin<V>(base, plane, izp, s); add_bond<V>(j, s, h);
+    load_bond<PREC>(b.J, jb + 2 * size_t(N) + izm, j); load_spin<V>(base, plane, izm, s); add_bond<V>(j, s, h);
+
+    if constexpr (KIND == kHB) {
+      const uint32_t t = p.counters[0];
+      const int sg = b.sample_ids[sb];
+      const uint32_t lat0 = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(g * V);
+      const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), lat0 >> 1, t, kTagHeatBath), p.key);
+      float out[3][V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const uint32_t lat = lat0 + v;
+        const float beta = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + g * V + v]];
+        const uint32_t w0 = (lat & 1u) ? w.z : w.x;
+        const uint32_t w1 = (lat & 1u) ? w.w : w.y;
+        heat_bath_draw(h[0][v], h[1][v], h[2][v], beta, w0, w1, out[0][v], out[1][v], out[2][v]);
+      }
+      store_spin<V>(base, plane, i, out);
+    } else {
+      float o[3][V];
+      load_spin<V>(base, plane, i, o);
+      if constexpr (KIND == kOR) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) overrelax(h[0][v], h[1][v], h[2][v], o[0][v], o[1][v], o[2][v]);
+        store_spin<V>(base, plane, i, o);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) e_acc[v] = fmaf(o[0][v], h[0][v], fmaf(o[1][v], h[1][v], o[2][v] * h[2][v]));
+    }
+  }
+
+  if (p.e_partial != nullptr) {
+    __shared__ double red[V][kSweepThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const double d = warp_sum(-static_cast<double>(e_acc[v]));
+      if (lane == 0) red[v][warp] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < V) {
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kSweepThreads / 32; ++w) acc += red[threadIdx.x][w];
+      const size_t lat_local = static_cast<size_t>(sb) * p.R + g * V + threadIdx.x;
+      p.e_partial[lat_local * p.chunks + chunk] = acc;
+    }
+  }
+}
+
+// E[sample*R + slot] = sum of the chunk partials of that lattice, one warp per
+// lattice, fixed summation order.
+__global__ void k_energy_finalize(const double* __restrict__ partial, int chunks, int n_lat,
+                                  const int* __restrict__ sample_ids, int R, double* __restrict__ E) {
+  const int lat = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (lat >= n_lat) return;
+  double acc = 0.0;
+  for (int c = lane; c < chunks; c += 32) acc += partial[static_cast<size_t>(lat) * chunks + c];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const int sb = lat / R, slot = lat - sb * R;
+    E[static_cast<size_t>(sample_ids[sb]) * R + slot] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parallel tempering (App. A.1): one thread per replica set.
+// ---------------------------------------------------------------------------
+__global__ void k_pt_sweep(int n_sets, int n_rep, int NT, int R, const double* __restrict__ beta,
+                           const double* __restrict__ E, int* __restrict__ perm,
+                           int* __restrict__ temp_of, long long* __restrict__ accepted, uint2 key,
+                           const uint32_t* __restrict__ counters) {
+  const int gset = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gset >= n_sets) return;
+  const int s = gset / n_rep;
+  int* pm = perm + static_cast<size_t>(gset) * NT;
+  const double* Es = E + static_cast<size_t>(s) * R;
+  const uint32_t t = counters[1];
+  const int acc_stride = NT > 1 ? NT - 1 : 1;
+  for (int k = 0; k + 1 < NT; ++k) {
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(gset), t,
+                                             kTagTempering), key);
+    const double r = uniform52(w.x, w.y);
+    const int a = pm[k], c = pm[k + 1];
+    const double delta = (beta[k] - beta[k + 1]) * (Es[a] - Es[c]);
+    if (delta >= 0.0 || r < exp(delta)) {
+      pm[k] = c;
+      pm[k + 1] = a;
+      accepted[static_cast<size_t>(gset) * acc_stride + k] += 1;
+    }
+  }
+  for (int k = 0; k < NT; ++k) temp_of[static_cast<size_t>(s) * R + pm[k]] = k;
+}
+
+__global__ void k_bump_counters(uint32_t* counters, uint32_t d_hb, uint32_t d_pt) {
+  counters[0] += d_hb;
+  counters[1] += d_pt;
+}
+
+// ---------------------------------------------------------------------------
+// Measurement (Sec. II.B).  One block per (sample, temperature k, replica
+// pair, chunk of sites).  Per site: q = s^a.s^b, the chiralities
+// zeta_mu = s_{x+mu}.(s_x x s_{x-mu}) of both replicas, kappa_mu = zeta^a
+// zeta^b, the Fourier sums at k = 0 and k_nu = 2 pi e_nu / L, and the
+// Schwinger-Dyson terms 2T s.h - h^2 + (s.h)^2 of both lattices.
+// Raw sums (kNQ = 30): [0] q, [1+2nu,2+2nu] q cos, q sin, [7+mu] kappa_mu,
+// [10+2(3mu+nu), 11+...] kappa_mu cos, sin, [28] SD_a, [29] SD_b.
+// FP32 within batches of sites, FP64 across batches and threads.
+// ---------------------------------------------------------------------------
+struct MeasureParams {
+  BucketView b;
+  int R, n_rep, NT, P, chunks;
+  const int* perm;      // [S][n_rep][NT]
+  const double* beta;   // [NT]
+  const float* phase;   // [L][2]: cos, sin of 2 pi x / L
+  double* partial;      // [S_b][NT][P][chunks][kNQ]
+};
+
+template <int V>
+__device__ __forceinline__ void load_one(const float* base, size_t plane, int i, float (&s)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) s[c] = __ldg(base + c * plane + static_cast<size_t>(i) * V);
+}
+
+__device__ __forceinline__ float triple(const float (&up)[3], const float (&a)[3], const float (&dn)[3]) {
+  const float cx = a[1] * dn[2] - a[2] * dn[1];
+  const float cy = a[2] * dn[0] - a[0] * dn[2];
+  const float cz = a[0] * dn[1] - a[1] * dn[0];
+  return fmaf(up[0], cx, fmaf(up[1], cy, up[2] * cz));
+}
+
+__device__ __forceinline__ void add_bond1(const float (&j)[6], const float (&s)[3], float (&h)[3]) {
+  h[0] = fmaf(j[0], s[0], fmaf(j[3], s[1], fmaf(j[4], s[2], h[0])));
+  h[1] = fmaf(j[3], s[0], fmaf(j[1], s[1], fmaf(j[5], s[2], h[1])));
+  h[2] = fmaf(j[4], s[0], fmaf(j[5], s[1], fmaf(j[2], s[2], h[2])));
+}
+
+template <int V, int PREC>
+__global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
+  extern __shared__ float sh_phase[];  // [L][2]
+  __shared__ double red[kMeasureThreads / 32][kNQ];
+  const BucketView& b = p.b;
+  const int L = b.L, N = b.N;
+  for (int t = threadIdx.x; t < 2 * L; t += blockDim.x) sh_phase[t] = p.phase[t];
+  __syncthreads();
+
+  const int unit = blockIdx.x / p.chunks;
+  const int chunk = blockIdx.x - unit * p.chunks;
+  const int pp = unit % p.P;
+  const int k = (unit / p.P) % p.NT;
+  const int sb = unit / (p.P * p.NT);
+  const int sg = b.sample_ids[sb];
+  const int slot_a = p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp) * p.NT + k];
+  const bool has_b = 2 * pp + 1 < p.n_rep;
+  const int slot_b = has_b ? p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp + 1) * p.NT + k] : slot_a;
+  const size_t plane = static_cast<size_t>(N) * V;
+  const float* base_a = b.spins + (static_cast<size_t>(sb) * b.G + slot_a / V) * 3 * plane + slot_a % V;
+  const float* base_b = b.spins + (static_cast<size_t>(sb) * b.G + slot_b / V) * 3 * plane + slot_b % V;
+  const double beta = p.beta[k];
+  const bool do_sd = beta > 0.0;
+  const float T = do_sd ? static_cast<float>(1.0 / beta) : 0.0f;
+  const size_t jb = static_cast<size_t>(sb) * 3 * N;
+
+  double acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+  float part[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) part[q] = 0.0f;
+
+  const int per_chunk = (N + p.chunks - 1) / p.chunks;
+  const int start = chunk * per_chunk;
+  const int end = min(N, start + per_chunk);
+  int batch = 0;
+  for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
+    const int x = i % L, y = (i / L) % L, z = i / (L * L);
+    const int LL = L * L;
+    const int nb[6] = {(x == L - 1) ? i - (L - 1) : i + 1, (x == 0) ? i + (L - 1) : i - 1,
+                       (y == L - 1) ? i - (L - 1) * L : i + L, (y == 0) ? i + (L - 1) * L : i - L,
+                       (z == L - 1) ? i - (L - 1) * LL : i + LL, (z == 0) ? i + (L - 1) * LL : i - LL};
+    float sa[3], sbv[3];
+    load_one<V>(base_a, plane, i, sa);
+    load_one<V>(base_b, plane, i, sbv);
+    float ha[3] = {0.f, 0.f, 0.f}, hb[3] = {0.f, 0.f, 0.f};
+    float za[3], zb[3];
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      float ua[3], da[3], ub[3], db[3];
+      load_one<V>(base_a, plane, nb[2 * mu], ua);
+      load_one<V>(base_a, plane, nb[2 * mu + 1], da);
+      load_one<V>(base_b, plane, nb[2 * mu], ub);
+      load_one<V>(base_b, plane, nb[2 * mu + 1], db);
+      za[mu] = triple(ua, sa, da);
+      zb[mu] = triple(ub, sbv, db);
+      if (do_sd) {
+        float j[6];
+        load_bond<PREC>(b.J, jb + static_cast<size_t>(mu) * N + i, j);
+        add_bond1(j, ua, ha);
+        add_bond1(j, ub, hb);
+        load_bond<PREC>(b.J, jb + static_cast<size_t>(mu) * N + nb[2 * mu + 1], j);
+        add_bond1(j, da, ha);
+        add_bond1(j, db, hb);
+      }
+    }
+    const float q = fmaf(sa[0], sbv[0], fmaf(sa[1], sbv[1], sa[2] * sbv[2]));
+    const float c[3] = {sh_phase[2 * x], sh_phase[2 * y], sh_phase[2 * z]};
+    const float s[3] = {sh_phase[2 * x + 1], sh_phase[2 * y + 1], sh_phase[2 * z + 1]};
+    part[0] += q;
+#pragma unroll
+    for (int nu = 0; nu < 3; ++nu) {
+      part[1 + 2 * nu] = fmaf(q, c[nu], part[1 + 2 * nu]);
+      part[2 + 2 * nu] = fmaf(q, s[nu], part[2 + 2 * nu]);
+    }
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      const float kap = za[mu] * zb[mu];
+      part[7 + mu] += kap;
+#pragma unroll
+      for (int nu = 0; nu < 3; ++nu) {
+        part[10 + 2 * (3 * mu + nu)] = fmaf(kap, c[nu], part[10 + 2 * (3 * mu + nu)]);
+        part[11 + 2 * (3 * mu + nu)] = fmaf(kap, s[nu], part[11 + 2 * (3 * mu + nu)]);
+      }
+    }
+    if (do_sd) {
+      const float sha = fmaf(sa[0], ha[0], fmaf(sa[1], ha[1], sa[2] * ha[2]));
+      const float hha = fmaf(ha[0], ha[0], fmaf(ha[1], ha[1], ha[2] * ha[2]));
+      const float shb = fmaf(sbv[0], hb[0], fmaf(sbv[1], hb[1], sbv[2] * hb[2]));
+      const float hhb = fmaf(hb[0], hb[0], fmaf(hb[1], hb[1], hb[2] * hb[2]));
+      part[28] += 2.0f * T * sha - (hha - sha * sha);
+      part[29] += 2.0f * T * shb - (hhb - shb * shb);
+    }
+    if (++batch == 8) {
+#pragma unroll
+      for (int qq = 0; qq < kNQ; ++qq) {
+        acc[qq] += static_cast<double>(part[qq]);
+        part[qq] = 0.0f;
+      }
+      batch = 0;
+    }
+  }
+#pragma unroll
+  for (int qq = 0; qq < kNQ; ++qq) acc[qq] += static_cast<double>(part[qq]);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int qq = 0; qq < kNQ; ++qq) {
+    const double d = warp_sum(acc[qq]);
+    if (lane == 0) red[warp][qq] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNQ) {
+    double sum = 0.0;
+    for (int w = 0; w < kMeasureThreads / 32; ++w) sum += red[w][threadIdx.x];
+    p.partial[(static_cast<size_t>(unit) * p.chunks + chunk) * kNQ + threadIdx.x] = sum;
+  }
+}
+
+// Turns the raw sums of one bucket into the accumulated observables:
+// one thread per (sample, temperature).
+__global__ void k_measure_finalize(const double* __restrict__ partial, const int* __restrict__ sample_ids,
+                                   int S_b, int NT, int P, int chunks, int n_rep, int R, int N,
+                                   const int* __restrict__ perm, const double* __restrict__ E,
+                                   double* __restrict__ obs, long long* __restrict__ counts) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= S_b * NT) return;
+  const int sb = u / NT, k = u - sb * NT;
+  const int sg = sample_ids[sb];
+  const double invN = 1.0 / N;
+  double* o = obs + (static_cast<size_t>(sg) * NT + k) * 9;
+  for (int pp = 0; pp < P; ++pp) {
+    double Q[kNQ];
+    for (int q = 0; q < kNQ; ++q) Q[q] = 0.0;
+    const size_t unit = (static_cast<size_t>(sb) * NT + k) * P + pp;
+    for (int c = 0; c < chunks; ++c)
+      for (int q = 0; q < kNQ; ++q) Q[q] += partial[(unit * chunks + c) * kNQ + q];
+    const bool has_b = 2 * pp + 1 < n_rep;
+    if (has_b) {
+      const double q0 = Q[0] * invN;
+      double q2k = 0.0;
+      for (int nu = 0; nu < 3; ++nu) {
+        const double re = Q[1 + 2 * nu] * invN, im = Q[2 + 2 * nu] * invN;
+        q2k += re * re + im * im;
+      }
+      double c2 = 0.0, c4 = 0.0, c2k = 0.0;
+      for (int mu = 0; mu < 3; ++mu) {
+        const double c0 = Q[7 + mu] * invN;
+        c2 += c0 * c0;
+        c4 += c0 * c0 * c0 * c0;
+        for (int nu = 0; nu < 3; ++nu) {
+          const double re = Q[10 + 2 * (3 * mu + nu)] * invN, im = Q[11 + 2 * (3 * mu + nu)] * invN;
+          c2k += re * re + im * im;
+        }
+      }
+      o[2] += q0 * q0;
+      o[3] += q0 * q0 * q0 * q0;
+      o[4] += q2k / 3.0;
+      o[5] += c2 / 3.0;
+      o[6] += c4 / 3.0;
+      o[7] += c2k / 9.0;
+      o[8] += (Q[28] + Q[29]) * invN;
+    } else {
+      o[8] += Q[28] * invN;
+    }
+  }
+  for (int r = 0; r < n_rep; ++r) {
+    const int slot = perm[(static_cast<size_t>(sg) * n_rep + r) * NT + k];
+    const double e = E[static_cast<size_t>(sg) * R + slot] * invN;
+    o[0] += e;
+    o[1] += e * e;
+  }
+  counts[static_cast<size_t>(sg) * NT + k] += 1;
+}
+
+// Host spins [N][3] (staged on the device) <-> one lane of the device layout.
+__global__ void k_scatter_spins(const float* __restrict__ stage, float* __restrict__ base, int N, int V, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t plane = static_cast<size_t>(N) * V;
+  for (int c = 0; c < 3; ++c) base[c * plane + static_cast<size_t>(i) * V + v] = stage[3 * static_cast<size_t>(i) + c];
+}
+
+__global__ void k_gather_spins(const float* __restrict__ base, float* __restrict__ stage, int N, int V, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t plane = static_cast<size_t>(N) * V;
+  for (int c = 0; c < 3; ++c) stage[3 * static_cast<size_t>(i) + c] = base[c * plane + static_cast<size_t>(i) * V + v];
+}
+
+__global__ void k_fill_spins(float* __restrict__ spins, size_t n_per_comp_block, size_t total) {
+  // Sets every spin to (0,0,1): component 2 planes to 1, others to 0.
+  const size_t idx = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const size_t comp = (idx / n_per_comp_block) % 3;
+  spins[idx] = comp == 2 ? 1.0f : 0.0f;
+}
+
+__global__ void k_philox_eval(const uint32_t* __restrict__ in, long n, uint32_t* __restrict__ out) {
+  const long r = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t* q = in + 6 * r;
+  const uint4 w = philox4x32_10(make_uint4(q[0], q[1], q[2], q[3]), make_uint2(q[4], q[5]));
+  out[4 * r + 0] = w.x;
+  out[4 * r + 1] = w.y;
+  out[4 * r + 2] = w.z;
+  out[4 * r + 3] = w.w;
+}
+
+}  // namespace hsg

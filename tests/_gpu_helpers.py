@@ -1,0 +1,97 @@
+"""Shared set-up for the GPU parity tests: build a context from seeded
+synthetic inputs and compare its state with the oracle."""
+import numpy as np
+
+import hsg_inputs as gi
+import oracle
+import paper_1309_1599_b300 as hsg
+
+SEED = 1
+# the benchmark spec tolerance: max |ds| per site after one sweep from identical input
+SWEEP_TOL = 2e-5
+# Heat-bath sites whose field direction lies within this distance of the
+# equator h_z = 0, where the azimuthal frame of the draw (Duff et al.) changes
+# sign, are compared on what is unique -- the polar part u = s.h/|h| and the
+# norm -- because binary32 and binary64 may legitimately pick different frames.
+FRAME_EPS = 1e-4
+
+
+def make(Ls, beta, n_rep=2, prec=hsg.F32, layout=hsg.PLAIN, n_or=8, measure_every=0,
+         seed=SEED, law="gaussian"):
+    """Context with couplings and random spins from hsg_inputs; returns
+    (lattice, couplings per sample as stored, float32 [N,3,6])."""
+    Ls = [Ls] if np.isscalar(Ls) else list(Ls)
+    lat = hsg.Lattice(Ls, beta, n_replicas=n_rep, coupling_prec=prec, layout=layout,
+                      n_or=n_or, measure_every=measure_every, seed=seed)
+    pstr = "f16" if prec == hsg.F16 else "f32"
+    J = []
+    for s, L in enumerate(Ls):
+        J6 = (gi.couplings(L, seed, s, law=law, precision=pstr) if law != "ferro"
+              else gi.ferromagnet(L))
+        lat.set_couplings(s, J6)
+        J.append(J6)
+        for slot in range(lat.R):
+            lat.set_spins(s, slot, gi.random_spins(L, seed, s, slot))
+    return lat, J
+
+
+def state(lat):
+    """All spins as float64 arrays [sample][slot] of shape [N,3]."""
+    return [[lat.get_spins(s, j).astype(np.float64) for j in range(lat.R)]
+            for s in range(lat.S)]
+
+
+def temp_of(lat):
+    perm = lat.get_perm()
+    t = np.empty((lat.S, lat.R), dtype=np.int64)
+    for s in range(lat.S):
+        for r in range(lat.n_replicas):
+            t[s, perm[s, r]] = np.arange(lat.NT)
+    return t
+
+
+def colours(L):
+    i = np.arange(L ** 3)
+    return (i % L + (i // L) % L + i // (L * L)) % 2
+
+
+def compare_sweep(lat, J, before, after, kind, hb_t):
+    """Per-half-sweep parity of one GPU sweep: the black half against the
+    oracle's black half from `before`; the white half against the oracle's
+    white half applied to the GPU's new black spins.  Returns
+    (max |ds| over all compared components, number of frame-ambiguous sites,
+    max |du| over those sites)."""
+    tmp = temp_of(lat)
+    worst, n_amb, worst_u = 0.0, 0, 0.0
+    for s, L in enumerate(lat.Ls):
+        J9 = oracle.j9_from_j6(J[s])
+        col = colours(L)
+        for slot in range(lat.R):
+            beta = float(lat.beta[tmp[s, slot]])
+            lid = s * lat.R + slot
+            ref = before[s][slot].copy()
+            h = oracle.fields(L, J9, ref, 0)
+            oracle.half_sweep(L, J9, ref, 0, kind, beta, lat.seed, lid, hb_t)
+            mixed = np.where((col == 0)[:, None], after[s][slot], before[s][slot])
+            mixed = np.ascontiguousarray(mixed)
+            h += oracle.fields(L, J9, mixed, 1)
+            oracle.half_sweep(L, J9, mixed, 1, kind, beta, lat.seed, lid, hb_t)
+            ref = np.where((col == 0)[:, None], ref, mixed)
+            got = after[s][slot]
+            amb = np.zeros(L ** 3, dtype=bool)
+            if kind == oracle.HB:
+                hn = np.linalg.norm(h, axis=1)
+                amb = np.abs(h[:, 2]) < FRAME_EPS * hn
+                if amb.any():
+                    hh = h[amb] / hn[amb, None]
+                    du = np.abs(((got[amb] - ref[amb]) * hh).sum(1)).max()
+                    worst_u = max(worst_u, float(du))
+                    assert np.abs(np.linalg.norm(got[amb], axis=1) - 1).max() < 1e-5
+                    n_amb += int(amb.sum())
+            if (~amb).any():
+                worst = max(worst, float(np.abs(got[~amb] - ref[~amb]).max()))
+    return worst, n_amb, worst_u
+
+
+def max_diff(a, b):
+    return max(float(np.abs(x - y).max()) for ra, rb in zip(a, b) for x, y in zip(ra, rb))

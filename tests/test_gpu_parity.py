@@ -1,0 +1,249 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Per-sweep parity: from identical input states and identical Philox streams,
+one GPU sweep and one oracle sweep agree per site within 2e-5 (max |ds|),
+checked over 10 consecutive sweeps (the oracle restarted from the GPU's state
+before each sweep).  Heat-bath sweeps are also compared free-running.
+Integer work (Philox words, PT labels and acceptance counts) is bit-exact.
+Sizes span several thread blocks with a ragged tail, mixed L, both layouts
+and both coupling precisions.
+"""
+import numpy as np
+import pytest
+
+import hsg_inputs as gi
+import oracle
+import paper_1309_1599_b300 as hsg
+from _gpu_helpers import SWEEP_TOL, compare_sweep, make, max_diff, state, temp_of
+
+pytestmark = pytest.mark.gpu
+
+
+def test_device_philox_matches_oracle_bitwise():
+    rng = np.random.default_rng(0)
+    rows = rng.integers(0, 2**32, size=(20000, 6), dtype=np.uint64).astype(np.uint32)
+    rows[:100, :4] = 0                       # zero counters
+    rows[100:200, 4:] = 0xFFFFFFFF           # all-ones keys
+    dev = hsg.philox4x32_10(rows)
+    ref = np.stack([oracle.philox4x32(r[:4], r[4:])[0] for r in rows])
+    assert np.array_equal(dev, ref)
+
+
+@pytest.mark.parametrize("prec", [hsg.F32, hsg.F16])
+@pytest.mark.parametrize("layout", [hsg.PLAIN, hsg.BATCHED])
+def test_couplings_and_spins_roundtrip(prec, layout):
+    lat, J = make([6, 8], [0.5, 1.0], n_rep=2, prec=prec, layout=layout)
+    for s, L in enumerate([6, 8]):
+        assert np.array_equal(lat.get_couplings(s), J[s])
+        for slot in range(lat.R):
+            assert np.array_equal(lat.get_spins(s, slot), gi.random_spins(L, 1, s, slot))
+
+
+CASES = [
+    # (Ls, betas, n_rep, prec, layout)
+    ([8], [2.0], 2, hsg.F32, hsg.PLAIN),                 # the L=8, T=0.5 plain workload
+    ([8], [2.0], 2, hsg.F32, hsg.BATCHED),
+    ([12, 8], [0.7, 1.9, 4.0], 2, hsg.F16, hsg.BATCHED),  # mixed L, ragged blocks
+    ([6], [0.0, 1.0, 5.0], 3, hsg.F16, hsg.PLAIN),         # beta = 0, odd replicas
+    ([4], [1.3], 1, hsg.F32, hsg.PLAIN),                   # smallest lattice
+    ([16], [1.0, 6.0], 2, hsg.F16, hsg.PLAIN),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_per_sweep_parity_ten_sweeps(case):
+    Ls, betas, n_rep, prec, layout = CASES[case]
+    lat, J = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout)
+    kinds = [oracle.HB] + [oracle.OR] * 8 + [oracle.HB]
+    worst, n_amb, n_sites = 0.0, 0, 0
+    for kind in kinds:
+        hb_t = int(lat.get_counters()[0])
+        before = state(lat)
+        if kind == oracle.HB:
+            lat.sweep_hb(1)
+        else:
+            lat.sweep_or(1)
+        after = state(lat)
+        d, amb, du = compare_sweep(lat, J, before, after, kind, hb_t)
+        worst = max(worst, d)
+        n_amb += amb
+        n_sites += lat.R * sum(L ** 3 for L in Ls)
+        assert d <= SWEEP_TOL, (kind, d)
+        assert du <= SWEEP_TOL, (kind, du)
+    assert worst > 0.0          # the two sides really are different programs
+    assert n_amb <= max(3, 1e-3 * n_sites)
+
+
+def test_heat_bath_free_running_ten_sweeps():
+    lat, J = make([8], [2.0], n_rep=2)
+    ref = state(lat)
+    for t in range(10):
+        lat.sweep_hb(1)
+        for slot in range(lat.R):
+            oracle.sweep(8, oracle.j9_from_j6(J[0]), ref[0][slot], oracle.HB, 2.0, lat.seed, slot, t)
+    assert max_diff(state(lat), ref) <= SWEEP_TOL
+
+
+def test_energies_match_oracle_on_the_same_state():
+    lat, J = make([12, 8], [0.5, 2.0], n_rep=2, prec=hsg.F16, layout=hsg.BATCHED)
+    lat.sweep_hb(2)
+    lat.sweep_or(3)         # energies fused into the last white half-sweep
+    E_fused = lat.get_energies()
+    lat.energy()            # standalone evaluation
+    E_direct = lat.get_energies()
+    st = state(lat)
+    for s, L in enumerate([12, 8]):
+        J9 = oracle.j9_from_j6(J[s])
+        for slot in range(lat.R):
+            ref = oracle.energy(L, J9, st[s][slot])
+            assert abs(E_fused[s, slot] - ref) <= 2e-6 * abs(ref)
+            assert abs(E_direct[s, slot] - ref) <= 2e-6 * abs(ref)
+
+
+def test_ferromagnet_energies_seven_digits():
+    """App. A.4.3: with ferromagnetic couplings the GPU energies equal an
+    independent CPU program's to the 7th significant digit."""
+    L = 8
+    lat, J = make([L], [2.0], n_rep=2, law="ferro")
+    up = np.zeros((L ** 3, 3), dtype=np.float32)
+    up[:, 2] = 1.0
+    for slot in range(lat.R):
+        lat.set_spins(0, slot, up)
+    lat.run_steps(3)
+    E = lat.get_energies()
+    st = state(lat)
+    J9 = oracle.j9_from_j6(J[0])
+    for slot in range(lat.R):
+        ref = oracle.energy(L, J9, st[0][slot])
+        assert abs(E[0, slot] - ref) <= 5e-8 * abs(ref), (E[0, slot], ref)
+        assert -3 * L ** 3 < ref < -2.0 * L ** 3     # ordered at T = 0.5
+
+
+def test_pt_labels_bit_exact():
+    betas = gi.linear_betas(0.2, 1.5, 7)
+    lat, J = make([6, 6, 6], betas, n_rep=3)
+    rng = np.random.default_rng(4)
+    N = 216
+    perm = lat.get_perm().copy()
+    acc = np.zeros((3, 3, 6), dtype=np.int64)
+    for t in range(40):
+        E = rng.normal(-1.5 * N, 0.05 * N, size=(3, lat.R))
+        lat.set_energies(E)
+        lat.pt_swap()
+        for s in range(3):
+            for r in range(3):
+                oracle.pt_sweep(betas, E[s], perm[s, r], lat.seed, s * 3 + r, t, acc[s, r])
+        assert np.array_equal(lat.get_perm(), perm)
+    assert np.array_equal(lat.get_pt_accepts(), acc)
+    assert 0 < acc.sum() < 40 * 54
+
+
+def _oracle_measure(lat, J, st, E):
+    obs = np.zeros((lat.S, lat.NT, hsg.NOBS))
+    perm = lat.get_perm()
+    for s, L in enumerate(lat.Ls):
+        N = L ** 3
+        J9 = oracle.j9_from_j6(J[s])
+        for k in range(lat.NT):
+            for r in range(lat.n_replicas):
+                slot = perm[s, r, k]
+                e = E[s, slot] / N
+                obs[s, k, 0] += e
+                obs[s, k, 1] += e * e
+                if lat.beta[k] > 0:
+                    obs[s, k, 8] += oracle.sd_residual(L, J9, st[s][slot], 1 / lat.beta[k])
+            for p in range(0, lat.n_replicas - 1, 2):
+                obs[s, k, 2:8] += oracle.measure_pair(L, st[s][perm[s, p, k]], st[s][perm[s, p + 1, k]])
+    return obs
+
+
+@pytest.mark.parametrize("layout", [hsg.PLAIN, hsg.BATCHED])
+def test_measurement_matches_oracle(layout):
+    betas = [0.0, 0.8, 3.0]
+    lat, J = make([12, 8], betas, n_rep=4, prec=hsg.F16, layout=layout)
+    lat.run_steps(4)
+    lat.reset_observables()
+    lat.measure()
+    obs, counts = lat.read_observables()
+    ref = _oracle_measure(lat, J, state(lat), lat.get_energies())
+    assert np.all(counts == 1)
+    assert np.allclose(obs[..., :2], ref[..., :2], rtol=1e-12, atol=0)   # from the same E
+    scale = np.abs(ref).max(axis=(0, 1)) + 1e-30
+    assert np.all(np.abs(obs - ref) <= 2e-5 * scale + 1e-9), np.abs(obs - ref).max(axis=(0, 1))
+
+
+def test_run_steps_is_the_step_composition():
+    """The graph-replayed step equals the explicit call sequence bit for bit."""
+    betas = gi.linear_betas(0.3, 1.0, 4)
+    a, _ = make([8, 12], betas, n_rep=2, prec=hsg.F16, layout=hsg.BATCHED, n_or=3, measure_every=2)
+    b, _ = make([8, 12], betas, n_rep=2, prec=hsg.F16, layout=hsg.BATCHED, n_or=3, measure_every=2)
+    a.run_steps(6)
+    for step in range(1, 7):
+        b.sweep_hb(1)
+        b.sweep_or(3)
+        b.pt_swap()
+        if step % 2 == 0:
+            b.measure()
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.get_perm(), b.get_perm())
+    oa, ca = a.read_observables()
+    ob, cb = b.read_observables()
+    assert np.array_equal(oa, ob) and np.array_equal(ca, cb)
+    assert ca.min() == 3
+    assert list(a.get_counters()) == [6, 6, 6]
+
+
+def test_run_step_matches_oracle_step_from_equilibrium():
+    """One whole Monte Carlo step (HB + 8 OR + energies + PT) from an
+    equilibrated state: spins within the per-sweep tolerance accumulated
+    over the step's 9 sweeps, labels identical."""
+    betas = gi.linear_betas(0.5, 1.0, 3)
+    lat, J = make([8], betas, n_rep=2)
+    lat.run_steps(200)
+    st = state(lat)
+    perm0 = lat.get_perm()
+    hb_t, pt_t, steps = (int(x) for x in lat.get_counters())
+    smp = oracle.Sample(8, J[0], np.stack(st[0]), betas, 2, lat.seed)
+    smp.perm[:] = perm0.reshape(-1)
+    smp.hb_t[0], smp.pt_t[0], smp.steps[0] = hb_t, pt_t, steps
+    lat.run_steps(1)
+    smp.run(1, 8, 0)
+    assert np.array_equal(lat.get_perm().reshape(-1), smp.perm)
+    d = max(np.abs(lat.get_spins(0, j) - smp.spins[j]).max() for j in range(lat.R))
+    assert d < 1e-3, d
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    betas = gi.linear_betas(0.3, 1.0, 4)
+    a, _ = make([8], betas, n_rep=2, layout=hsg.BATCHED, measure_every=1)
+    a.run_steps(3)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.run_steps(3)
+    b = hsg.Lattice([8], betas, n_replicas=2, layout=hsg.BATCHED, measure_every=1, seed=a.seed)
+    b.load(path)
+    b.run_steps(3)
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.read_observables()[0], b.read_observables()[0])
+    assert np.array_equal(a.get_counters(), b.get_counters())
+
+
+def test_mismatched_checkpoint_rejected(tmp_path):
+    a, _ = make([8], [1.0], n_rep=2)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    b = hsg.Lattice([6], [1.0], n_replicas=2)
+    with pytest.raises(hsg.HsgError, match="EINVAL"):
+        b.load(path)
+
+
+def test_or_conserves_energy_and_norm_on_gpu():
+    lat, _ = make([16], [1.0], n_rep=2, prec=hsg.F16, layout=hsg.BATCHED)
+    lat.energy()
+    E0 = lat.get_energies()
+    lat.sweep_or(50)
+    E1 = lat.get_energies()
+    assert np.all(np.abs(E1 - E0) <= 1e-4 * np.abs(E0))
+    for slot in range(lat.R):
+        n = np.linalg.norm(lat.get_spins(0, slot), axis=1)
+        assert np.abs(n - 1).max() < 1e-4
