@@ -193,6 +193,34 @@ hsg_status hsg_synchronize(hsg_t h);
  * generator against other implementations. */
 hsg_status hsg_philox4x32_10(const uint32_t *in, long n, uint32_t *out);
 
+/* Energies without any allocation by the library.  The paper has no
+ * counterpart to this call; it exists for callers that cannot let a library
+ * call cudaMalloc or cudaFree -- hosts that give out device memory only from
+ * an arena they plan themselves, or latency-critical loops that must never
+ * wait in the driver's allocator.
+ *   spins  device float [n_samples*lattices_per_sample][3][N]: component
+ *          planes of each lattice, site i = x + L*(y + L*z), lattices of a
+ *          sample consecutive;
+ *   J6     device float [n_samples][3][N][6]: bond (i, i+e_mu) of each sample
+ *          at [mu][i], entries (xx,yy,zz,xy,xz,yz);
+ *   E_out  device double [n_samples*lattices_per_sample], receives
+ *          E = -sum_bonds s_x^T J s_y (FP32 terms, FP64 sums);
+ *   stream cudaStream_t to run on (NULL = legacy default stream).
+ * All three buffers belong to the caller.  The work is enqueued
+ * asynchronously.  The only working memory is a fixed device array of
+ * HSG_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) inside the library, which every
+ * GPU that loads the library holds until the process exits; a request needing
+ * more than that (lattices x ceil(L^3/512) partial sums) is rejected with
+ * HSG_EINVAL before anything runs.  The first call on each device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (each call writes every entry it reads, so
+ * nothing needs clearing), so calls that overlap on the GPU race and give
+ * wrong results: order them on one stream. */
+#define HSG_NOALLOC_SCRATCH_DOUBLES 262144
+hsg_status hsg_energy_noalloc(const float *spins, const float *J6, int L, int n_samples,
+                              int lattices_per_sample, double *E_out, void *stream);
+
 /* Message of the last failure in the calling thread ("" if none). */
 const char *hsg_last_error(void);
 

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhsg.so")
-SOURCES = [os.path.join(CSRC, "hsg.cu")]
+SOURCES = [os.path.join(CSRC, "hsg.cu"), os.path.join(CSRC, "hsg_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(ROOT, "include", "hsg.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -50,6 +50,10 @@ struct Bucket {
 
 }  // namespace
 
+// Lets the other translation units of the library report through
+// hsg_last_error().
+void hsg_record_error(const std::string& msg) { g_last_error = msg; }
+
 struct hsg_ctx {
   int S = 0, n_rep = 0, NT = 0, R = 0, V = 1, prec = HSG_F32, layout = 0, n_or = 0;
   int measure_every = 0;

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
 
 // E[sample*R + slot] = sum of the chunk partials of that lattice, one warp per
 // lattice, fixed summation order.
-__global__ void k_energy_finalize(const double* __restrict__ partial, int chunks, int n_lat,
+static __global__ void k_energy_finalize(const double* __restrict__ partial, int chunks, int n_lat,
                                   const int* __restrict__ sample_ids, int R, double* __restrict__ E) {
   const int lat = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -288,7 +288,7 @@ __global__ void k_energy_finalize(const double* __restrict__ partial, int chunks
 // ---------------------------------------------------------------------------
 // Parallel tempering (App. A.1): one thread per replica set.
 // ---------------------------------------------------------------------------
-__global__ void k_pt_sweep(int n_sets, int n_rep, int NT, int R, const double* __restrict__ beta,
+static __global__ void k_pt_sweep(int n_sets, int n_rep, int NT, int R, const double* __restrict__ beta,
                            const double* __restrict__ E, int* __restrict__ perm,
                            int* __restrict__ temp_of, long long* __restrict__ accepted, uint2 key,
                            const uint32_t* __restrict__ counters) {
@@ -314,7 +314,7 @@ __global__ void k_pt_sweep(int n_sets, int n_rep, int NT, int R, const double* _
   for (int k = 0; k < NT; ++k) temp_of[static_cast<size_t>(s) * R + pm[k]] = k;
 }
 
-__global__ void k_bump_counters(uint32_t* counters, uint32_t d_hb, uint32_t d_pt) {
+static __global__ void k_bump_counters(uint32_t* counters, uint32_t d_hb, uint32_t d_pt) {
   counters[0] += d_hb;
   counters[1] += d_pt;
 }
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
 
 // Turns the raw sums of one bucket into the accumulated observables:
 // one thread per (sample, temperature).
-__global__ void k_measure_finalize(const double* __restrict__ partial, const int* __restrict__ sample_ids,
+static __global__ void k_measure_finalize(const double* __restrict__ partial, const int* __restrict__ sample_ids,
                                    int S_b, int NT, int P, int chunks, int n_rep, int R, int N,
                                    const int* __restrict__ perm, const double* __restrict__ E,
                                    double* __restrict__ obs, long long* __restrict__ counts) {
@@ -534,21 +534,21 @@ __global__ void k_measure_finalize(const double* __restrict__ partial, const int
 }
 
 // Host spins [N][3] (staged on the device) <-> one lane of the device layout.
-__global__ void k_scatter_spins(const float* __restrict__ stage, float* __restrict__ base, int N, int V, int v) {
+static __global__ void k_scatter_spins(const float* __restrict__ stage, float* __restrict__ base, int N, int V, int v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const size_t plane = static_cast<size_t>(N) * V;
   for (int c = 0; c < 3; ++c) base[c * plane + static_cast<size_t>(i) * V + v] = stage[3 * static_cast<size_t>(i) + c];
 }
 
-__global__ void k_gather_spins(const float* __restrict__ base, float* __restrict__ stage, int N, int V, int v) {
+static __global__ void k_gather_spins(const float* __restrict__ base, float* __restrict__ stage, int N, int V, int v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const size_t plane = static_cast<size_t>(N) * V;
   for (int c = 0; c < 3; ++c) stage[3 * static_cast<size_t>(i) + c] = base[c * plane + static_cast<size_t>(i) * V + v];
 }
 
-__global__ void k_fill_spins(float* __restrict__ spins, size_t n_per_comp_block, size_t total) {
+static __global__ void k_fill_spins(float* __restrict__ spins, size_t n_per_comp_block, size_t total) {
   // Sets every spin to (0,0,1): component 2 planes to 1, others to 0.
   const size_t idx = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= total) return;
@@ -556,7 +556,7 @@ __global__ void k_fill_spins(float* __restrict__ spins, size_t n_per_comp_block,
   spins[idx] = comp == 2 ? 1.0f : 0.0f;
 }
 
-__global__ void k_philox_eval(const uint32_t* __restrict__ in, long n, uint32_t* __restrict__ out) {
+static __global__ void k_philox_eval(const uint32_t* __restrict__ in, long n, uint32_t* __restrict__ out) {
   const long r = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const uint32_t* q = in + 6 * r;
