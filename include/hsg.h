@@ -70,6 +70,16 @@ enum { HSG_F32 = 0, HSG_F16 = 1 };
  *                       read (requires R even). */
 enum { HSG_LAYOUT_PLAIN = 0, HSG_LAYOUT_BATCHED = 1 };
 
+/* Sweep kernel.
+ *   HSG_SWEEP_AUTO      one fused pass per sweep (both colours, each spin read
+ *                       and written once, planes staged in shared memory),
+ *                       wherever the lattice size allows it (whole planes, or
+ *                       bands of at least 8 rows that divide L); the two-pass
+ *                       kernel otherwise.  Doubles the spin memory.
+ *   HSG_SWEEP_TWO_PASS  always one kernel per colour half-sweep.
+ * Both give the same spins bit for bit. */
+enum { HSG_SWEEP_AUTO = 0, HSG_SWEEP_TWO_PASS = 1 };
+
 /* Observables accumulated per (sample, temperature index) by hsg_measure
  * (Sec. II.B).  Per measurement, with e = E/N:
  *   [0] sum of e, [1] sum of e^2      over the n_replicas lattices at that T
@@ -95,7 +105,9 @@ typedef struct {
   int measure_every;      /* hsg_run_steps measures every this many steps (0: never) */
   uint64_t seed;          /* Philox key */
   void *stream;           /* cudaStream_t to use; NULL = the legacy default stream */
-  long long timeout_cycles; /* bound for device-side waits, 0 = library default */
+  long long timeout_cycles; /* bound (SM clock cycles) for each device-side wait,
+                              0 = library default (4e9) */
+  int sweep_kernel;       /* HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS */
 } hsg_config;
 
 /* Create a context: validates cfg (copied; the caller's arrays may be freed
@@ -185,8 +197,17 @@ hsg_status hsg_get_launch_count(hsg_t h, uint64_t *out);
 hsg_status hsg_save(hsg_t h, const char *path);
 hsg_status hsg_load(hsg_t h, const char *path);
 
-/* Wait for all work enqueued by h. */
+/* Wait for all work enqueued by h.  HSG_ETIMEOUT if a kernel's bounded
+ * device-side wait gave up since the last check. */
 hsg_status hsg_synchronize(hsg_t h);
+
+/* Exercises the failure path of the bounded device-side waits: launches one
+ * fused sweep that first waits, with the given bound, on a barrier nothing
+ * completes; the kernel records the expiry, waits for its own copies in
+ * flight and returns without writing spins.  Returns HSG_ETIMEOUT when the
+ * mechanism works (the context stays usable and unchanged); HSG_ESTATE if no
+ * sample uses the fused sweep. */
+hsg_status hsg_selftest_wait_timeout(hsg_t h, long long timeout_cycles);
 
 /* Philox4x32-10 evaluated on the device: in = host uint32 [n][6] rows
  * (c0,c1,c2,c3,k0,k1), out = host uint32 [n][4].  For checking the device

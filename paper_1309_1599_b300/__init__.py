@@ -17,10 +17,12 @@ import os
 import numpy as np
 
 __all__ = ["Lattice", "HsgError", "load_library", "philox4x32_10", "library_path",
-           "F32", "F16", "PLAIN", "BATCHED", "NOBS", "OBS_NAMES"]
+           "F32", "F16", "PLAIN", "BATCHED", "SWEEP_AUTO", "SWEEP_TWO_PASS", "NOBS",
+           "OBS_NAMES"]
 
 F32, F16 = 0, 1
 PLAIN, BATCHED = 0, 1
+SWEEP_AUTO, SWEEP_TWO_PASS = 0, 1
 NOBS = 9
 OBS_NAMES = ("e", "e2", "q2", "q4", "q2k", "c2", "c4", "c2k", "sd")
 _STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA",
@@ -47,7 +49,7 @@ class _Config(ctypes.Structure):
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("coupling_prec", ctypes.c_int),
                 ("layout", ctypes.c_int), ("n_or", ctypes.c_int), ("measure_every", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("timeout_cycles", ctypes.c_longlong)]
+                ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int)]
 
 
 _SIGNATURES = {
@@ -75,6 +77,7 @@ _SIGNATURES = {
     "hsg_save": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_load": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_synchronize": [ctypes.c_void_p],
+    "hsg_selftest_wait_timeout": [ctypes.c_void_p, ctypes.c_longlong],
     "hsg_philox4x32_10": [ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p],
 }
 
@@ -140,7 +143,7 @@ class Lattice:
 
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
-                 timeout_cycles=0):
+                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO):
         lib = load_library()
         _require_gpu()
         if np.isscalar(L):
@@ -167,6 +170,7 @@ class Lattice:
         cfg.seed = int(seed) & (2**64 - 1)
         cfg.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
         cfg.timeout_cycles = int(timeout_cycles)
+        cfg.sweep_kernel = int(sweep_kernel)
         h = ctypes.c_void_p()
         _check(lib.hsg_lattice_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -293,3 +297,7 @@ class Lattice:
 
     def synchronize(self) -> None:
         _check(self._lib.hsg_synchronize(self._h))
+
+    def selftest_wait_timeout(self, timeout_cycles: int) -> int:
+        """Status of hsg_selftest_wait_timeout (4 = HSG_ETIMEOUT expected)."""
+        return self._lib.hsg_selftest_wait_timeout(self._h, int(timeout_cycles))

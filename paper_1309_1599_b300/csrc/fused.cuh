@@ -1,0 +1,400 @@
+// Fused checkerboard sweep: one pass over the lattice updates every black
+// site and then every white site (App. A.1: black half with the old white
+// spins, white half with the new black spins), reading each spin once from
+// HBM and writing it once.
+//
+// A CTA owns one lattice group (V lattices of one sample) and a band of
+// `band_rows` rows y (all x), and marches through the planes z.  At step z it
+// updates the black sites of plane z and then the white sites of plane z-1:
+// black(z) needs the white spins of planes z-1, z, z+1 before they change,
+// white(z-1) needs the black spins of planes z-2, z-1, z after they changed.
+//   * Planes are staged in shared memory by 1-D bulk TMA copies
+//     (cp.async.bulk, mbarrier completion) into a ring of 4 slots, issued two
+//     planes ahead.  A slot holds the band plus two halo rows on each side.
+//   * Each thread owns one x-pair (2k, 2k+1) of one row: at every plane it
+//     holds one black and one white site.  The z-neighbours of its sites are
+//     its own sites at the neighbouring planes, kept in registers; shared
+//     memory serves only the in-plane neighbours (rows are stored
+//     parity-split, so these reads are contiguous across a warp).
+//   * Spins are read from one buffer and written to the other (ping-pong), so
+//     the halo rows of neighbouring bands and the periodic wrap in z are read
+//     unmodified.  The march covers planes 0..L+1; black(0) and black(1) are
+//     recomputed at the end (same inputs, same random numbers) for white(0).
+//   * Halo rows: the black sites of the rows just outside the band are
+//     updated too (not stored), because the band's white sites need them.
+//     With band_rows == L a CTA holds whole planes and rows wrap in y.
+//   * The field is summed in the same order as in k_sweep_half (+x, -x, +y,
+//     -y, +z, -z), so both kernels give the same spins bit for bit.
+//   * Waits on the TMA barriers are bounded (clock64); on expiry the kernel
+//     writes HSG_ETIMEOUT to *status, waits (bounded) for its copies in
+//     flight and returns; no thread ever spins without limit.
+#pragma once
+#include "kernels.cuh"
+
+namespace hsg {
+
+constexpr int kFusedMaxThreads = 640;
+constexpr int kFusedSlots = 4;
+constexpr int kStatusTimeout = 4;                 // value of HSG_ETIMEOUT
+constexpr long long kCleanupWait = 2000000000LL;  // cycles, per outstanding copy
+
+struct FusedParams {
+  const float* in;        // spins before the sweep, bucket layout
+  float* out;             // spins after the sweep
+  const void* J;
+  const int* sample_ids;  // [S_b] global sample index
+  int L, N, G, R;
+  int band_rows;          // rows written per CTA; == L for whole planes
+  int n_bands;            // L / band_rows
+  const int* temp_of;     // [S][R]
+  const float* beta_f;    // [N_T]
+  uint2 key;
+  const uint32_t* counters;
+  double* e_partial;      // [S_b*R][n_bands] or null
+  int* status;            // device status word
+  long long timeout;      // clock64 cycles for one wait
+  int probe_timeout;      // nonzero: first wait on a barrier nobody completes
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long timeout) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > timeout) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int V>
+__device__ __forceinline__ void lds_site(const float* p, float (&s)[3][V], int comp_stride) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (V == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p + c * comp_stride);
+      s[c][0] = t.x;
+      s[c][1] = t.y;
+    } else {
+      s[c][0] = p[c * comp_stride];
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void sts_site(float* p, const float (&s)[3][V], int comp_stride) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (V == 2) {
+      *reinterpret_cast<float2*>(p + c * comp_stride) = make_float2(s[c][0], s[c][1]);
+    } else {
+      p[c * comp_stride] = s[c][0];
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void stg_site(float* p, const float (&s)[3][V], size_t comp_stride) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (V == 2) {
+      *reinterpret_cast<float2*>(p + c * comp_stride) = make_float2(s[c][0], s[c][1]);
+    } else {
+      p[c * comp_stride] = s[c][0];
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) d[c][v] = s[c][v];
+}
+
+// Local field of the site of x-parity `a` in pair k of row y, plane pl:
+// h = sum over its six bonds of J s_neighbour (J symmetric).  `partner` is
+// the other site of the pair, `ext` the x-neighbour outside the pair, `yu`,
+// `yd`, `zu`, `zd` the neighbours at y+1, y-1, z+1, z-1.
+template <int V, int PREC>
+__device__ __forceinline__ void pair_field(const void* J, size_t jb, int N, int L, int half, int pl, int pl_dn,
+                                           int y, int y_dn, int a, int k, int k_dn, const float (&partner)[3][V],
+                                           const float (&ext)[3][V], const float (&yu)[3][V],
+                                           const float (&yd)[3][V], const float (&zu)[3][V],
+                                           const float (&zd)[3][V], float (&h)[3][V]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) h[c][v] = 0.0f;
+  const int row = (pl * L + y) * L;
+  const int pos = row + a * half + k;                            // this site
+  const int pos_xm = (a == 1) ? row + k : row + half + k_dn;     // site at x-1
+  float xp[3][V], xm[3][V];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xp[c][v] = (a == 0) ? partner[c][v] : ext[c][v];   // neighbour at x+1
+      xm[c][v] = (a == 0) ? ext[c][v] : partner[c][v];   // neighbour at x-1
+    }
+  float j[6];
+  load_bond<PREC>(J, jb + pos, j);
+  add_bond<V>(j, xp, h);
+  load_bond<PREC>(J, jb + pos_xm, j);
+  add_bond<V>(j, xm, h);
+  load_bond<PREC>(J, jb + N + pos, j);
+  add_bond<V>(j, yu, h);
+  load_bond<PREC>(J, jb + N + (pl * L + y_dn) * L + a * half + k, j);
+  add_bond<V>(j, yd, h);
+  load_bond<PREC>(J, jb + 2 * static_cast<size_t>(N) + pos, j);
+  add_bond<V>(j, zu, h);
+  load_bond<PREC>(J, jb + 2 * static_cast<size_t>(N) + (pl_dn * L + y) * L + a * half + k, j);
+  add_bond<V>(j, zd, h);
+}
+
+template <int KIND, int V>
+__device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3][V], const float (&beta)[V],
+                                            uint32_t i_nat, uint32_t lat0, uint32_t t, uint2 key) {
+  if constexpr (KIND == kHB) {
+    const uint4 w = philox4x32_10(make_uint4(i_nat, lat0 >> 1, t, kTagHeatBath), key);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const uint32_t lat = lat0 + v;
+      const uint32_t w0 = (lat & 1u) ? w.z : w.x;
+      const uint32_t w1 = (lat & 1u) ? w.w : w.y;
+      heat_bath_draw(h[0][v], h[1][v], h[2][v], beta[v], w0, w1, s[0][v], s[1][v], s[2][v]);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) overrelax(h[0][v], h[1][v], h[2][v], s[0][v], s[1][v], s[2][v]);
+  }
+}
+
+template <int KIND, int V, int PREC>
+__global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams p) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t bars[kFusedSlots + 1];  // [kFusedSlots]: never completed
+  __shared__ double s_red[V][kFusedMaxThreads / 32];
+
+  const int L = p.L, half = L >> 1, N = p.N;
+  const bool full = (p.band_rows == L);
+  const int slot_rows = full ? L : p.band_rows + 4;
+  const int row_f = L * V;                        // floats per staged row
+  const int comp_f = slot_rows * row_f;           // floats per component in a slot
+  const int slot_f = 3 * comp_f;
+  const int gi = blockIdx.x / p.n_bands;
+  const int band = blockIdx.x - gi * p.n_bands;
+  const int sb = gi / p.G, g = gi - sb * p.G;
+  const int y0 = band * p.band_rows;
+  const int tid = threadIdx.x;
+  const int rows_t = full ? L : p.band_rows + 2;
+  const bool active = tid < rows_t * half;
+  const int rt = active ? tid / half : 0;
+  const int k = active ? tid - rt * half : 0;
+  const int r = full ? rt : rt + 1;               // row within a slot
+  const int y = full ? rt : (y0 - 2 + r + L) % L; // lattice row
+  const bool owner = active && (full || (r >= 2 && r < p.band_rows + 2));
+  const int r_up = full ? (r + 1 == L ? 0 : r + 1) : r + 1;
+  const int r_dn = full ? (r == 0 ? L - 1 : r - 1) : r - 1;
+  const int k_up = (k + 1 == half) ? 0 : k + 1;
+  const int k_dn = (k == 0) ? half - 1 : k - 1;
+  const int y_dn = (y == 0) ? L - 1 : y - 1;
+  const size_t gbase = static_cast<size_t>(gi) * 3 * N * V;
+  const float* in_g = p.in + gbase;
+  float* out_g = p.out + gbase;
+  const size_t plane_g = static_cast<size_t>(N) * V;   // component stride in global memory
+  const size_t jb = static_cast<size_t>(sb) * 3 * N;
+
+  float beta[V];
+  uint32_t lat0 = 0, t_hb = 0;
+  if constexpr (KIND == kHB) {
+    const int sg = p.sample_ids[sb];
+    lat0 = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(g * V);
+    t_hb = p.counters[0];
+#pragma unroll
+    for (int v = 0; v < V; ++v) beta[v] = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + g * V + v]];
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) beta[v] = 0.0f;
+  }
+
+  const uint32_t slot_bytes = static_cast<uint32_t>(slot_f) * 4u;
+  const int ystart = full ? 0 : (y0 - 2 + L) % L;
+  // Virtual plane vp (from -1 to L+2) lives in slot (vp+1) & 3.
+  auto issue = [&](int vp) {
+    const int pl = (vp + L) % L;
+    const int s = (vp + 1) & 3;
+    float* dst = smem + s * slot_f;
+    mbar_expect_tx(&bars[s], slot_bytes);
+    for (int c = 0; c < 3; ++c) {
+      int done = 0;
+      while (done < slot_rows) {
+        const int yy = (ystart + done) % L;
+        const int n = min(slot_rows - done, L - yy);
+        const float* src = in_g + c * plane_g + (static_cast<size_t>(pl) * L + yy) * row_f;
+        bulk_copy_g2s(dst + c * comp_f + done * row_f, src, static_cast<uint32_t>(n * row_f * 4), &bars[s]);
+        done += n;
+      }
+    }
+  };
+  auto parity_of = [](int vp) -> uint32_t { return static_cast<uint32_t>(((vp + 1) >> 2) & 1); };
+  // Site (row rr, x-parity a, pair kk) of the slot holding virtual plane vp.
+  auto at = [&](int vp, int rr, int a, int kk) -> float* {
+    return smem + ((vp + 1) & 3) * slot_f + rr * row_f + (a * half + kk) * V;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s <= kFusedSlots; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int issued = -2;  // highest virtual plane issued (meaningful in thread 0)
+  if (tid == 0) {
+    for (int vp = -1; vp <= 2; ++vp) issue(vp);
+    issued = 2;
+  }
+
+  // Register window of this thread's pair: black / white sites at planes
+  // z-2 (black only), z-1, z, z+1.
+  float Bm2[3][V], Bm1[3][V], Wm1[3][V], B0[3][V], W0[3][V], Bp1[3][V], Wp1[3][V];
+  double e_acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) e_acc[v] = 0.0;
+
+  int first_unwaited = -1;  // lowest virtual plane not yet known complete
+  bool ok = true;
+  if (p.probe_timeout) ok = mbar_wait_bounded(&bars[kFusedSlots], 0, p.timeout);
+  ok = ok && mbar_wait_bounded(&bars[0], parity_of(-1), p.timeout);
+  ok = ok && mbar_wait_bounded(&bars[1], parity_of(0), p.timeout);
+  bool failed = __syncthreads_or(!ok) != 0;
+  if (!failed) first_unwaited = 1;
+  if (!failed && active) {
+    const int ab_m1 = (y + L - 1) & 1;  // black x-parity at plane L-1
+    lds_site<V>(at(-1, r, ab_m1, k), Bm1, comp_f);
+    lds_site<V>(at(-1, r, ab_m1 ^ 1, k), Wm1, comp_f);
+    const int ab_0 = y & 1;
+    lds_site<V>(at(0, r, ab_0, k), B0, comp_f);
+    lds_site<V>(at(0, r, ab_0 ^ 1, k), W0, comp_f);
+    copy3<V>(Bm2, Bm1);
+  }
+
+  for (int z = 0; !failed && z <= L + 1; ++z) {
+    ok = mbar_wait_bounded(&bars[(z + 2) & 3], parity_of(z + 1), p.timeout);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    first_unwaited = z + 2;
+    const int pz = z % L;
+    if (active) {
+      const int ab1 = (y + pz + 1) & 1;
+      lds_site<V>(at(z + 1, r, ab1, k), Bp1, comp_f);
+      lds_site<V>(at(z + 1, r, ab1 ^ 1, k), Wp1, comp_f);
+
+      // black site of plane z (x-parity ab) from the old white spins
+      const int ab = (y + pz) & 1;
+      const int pz_dn = (pz == 0) ? L - 1 : pz - 1;
+      float ext[3][V], yu[3][V], yd[3][V], h[3][V];
+      lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k_dn), ext, comp_f);
+      lds_site<V>(at(z, r_up, ab, k), yu, comp_f);
+      lds_site<V>(at(z, r_dn, ab, k), yd, comp_f);
+      pair_field<V, PREC>(p.J, jb, N, L, half, pz, pz_dn, y, y_dn, ab, k, k_dn, W0, ext, yu, yd, Wp1, Wm1, h);
+      const uint32_t i_nat = static_cast<uint32_t>(2 * k + ab + L * (y + L * pz));
+      update_site<KIND, V>(h, B0, beta, i_nat, lat0, t_hb, p.key);
+      sts_site<V>(at(z, r, ab, k), B0, comp_f);
+
+      // white site of plane z-1 from the new black spins
+      if (z >= 2 && owner) {
+        const int q = (z - 1) % L;
+        const int q_dn = (q == 0) ? L - 1 : q - 1;
+        const int aw = ((y + q) & 1) ^ 1;
+        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k_up : k_dn), ext, comp_f);
+        lds_site<V>(at(z - 1, r_up, aw, k), yu, comp_f);
+        lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
+        pair_field<V, PREC>(p.J, jb, N, L, half, q, q_dn, y, y_dn, aw, k, k_dn, Bm1, ext, yu, yd, B0, Bm2, h);
+        const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));
+        update_site<KIND, V>(h, Wm1, beta, iw_nat, lat0, t_hb, p.key);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          e_acc[v] += static_cast<double>(fmaf(Wm1[0][v], h[0][v], fmaf(Wm1[1][v], h[1][v], Wm1[2][v] * h[2][v])));
+        float* dst = out_g + (static_cast<size_t>(q * L + y) * L) * V;
+        stg_site<V>(dst + (static_cast<size_t>((aw ^ 1) * half + k)) * V, Bm1, plane_g);
+        stg_site<V>(dst + (static_cast<size_t>(aw * half + k)) * V, Wm1, plane_g);
+      }
+    }
+    // Generic-proxy accesses of the slot being refilled must precede the
+    // asynchronous copy that overwrites it.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && z + 3 <= L + 2) {
+      issue(z + 3);
+      issued = z + 3;
+    }
+    copy3<V>(Bm2, Bm1);
+    copy3<V>(Bm1, B0);
+    copy3<V>(Wm1, W0);
+    copy3<V>(B0, Bp1);
+    copy3<V>(W0, Wp1);
+  }
+
+  if (failed) {
+    // Record the expiry and wait (bounded) for this CTA's copies in flight
+    // before its shared memory is released.
+    if (tid == 0) {
+      atomicExch(p.status, kStatusTimeout);
+      for (int vp = first_unwaited; vp <= issued; ++vp)
+        mbar_wait_bounded(&bars[(vp + 1) & 3], parity_of(vp), kCleanupWait);
+    }
+    return;
+  }
+
+  if (p.e_partial != nullptr) {
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const double d = warp_sum(-e_acc[v]);
+      if (lane == 0) s_red[v][warp] = d;
+    }
+    __syncthreads();
+    if (tid < V) {
+      double acc = 0.0;
+      const int nw = (blockDim.x + 31) >> 5;
+      for (int w = 0; w < nw; ++w) acc += s_red[tid][w];
+      const size_t lat_local = static_cast<size_t>(sb) * p.R + g * V + tid;
+      p.e_partial[lat_local * p.n_bands + band] = acc;
+    }
+  }
+}
+
+}  // namespace hsg

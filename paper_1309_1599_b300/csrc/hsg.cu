@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/hsg.h"
+#include "fused.cuh"
 #include "kernels.cuh"
 
 using namespace hsg;
@@ -39,10 +40,14 @@ struct Bucket {
   int L = 0, N = 0, S_b = 0, G = 0;
   std::vector<int> samples;   // global sample ids, in order
   int* d_samples = nullptr;
-  float* d_spins = nullptr;   // [S_b][G][3][N][V]
+  float* d_spins[2] = {nullptr, nullptr};  // [S_b][G][3][N][V]; [1] only with the fused sweep
+  int cur = 0;                // which of d_spins holds the current spins
   void* d_J = nullptr;        // f32 [S_b][3][N][6] or f16 [S_b][3][N][8]
   int sweep_chunks = 0;       // blocks per lattice group in a half-sweep
-  double* d_epart = nullptr;  // [S_b*R][sweep_chunks]
+  bool fused = false;         // sweeps use k_sweep_fused (ping-pong buffers)
+  int band_rows = 0, n_bands = 0;  // fused-sweep tiling
+  size_t fused_smem = 0;      // dynamic shared memory of the fused sweep
+  double* d_epart = nullptr;  // [S_b*R][max(sweep_chunks, n_bands)]
   int m_chunks = 0, P = 0;
   double* d_mpart = nullptr;  // [S_b][NT][P][m_chunks][kNQ]
   float* d_phase = nullptr;   // [L][2]
@@ -77,8 +82,12 @@ struct hsg_ctx {
   uint32_t* d_tmp_u32 = nullptr;
   bool energy_valid = false;
   uint64_t counters[3] = {0, 0, 0};
-  cudaGraphExec_t g_step = nullptr, g_step_m = nullptr;
-  uint64_t g_step_launches = 0, g_step_m_launches = 0;  // kernels per graph replay
+  // Captured steps, by [parity of the fused buckets' buffer index][measure?].
+  cudaGraphExec_t g_step[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  uint64_t g_step_launches[2][2] = {{0, 0}, {0, 0}};  // kernels per graph replay
+  int* d_status = nullptr;     // device status word (HSG_ETIMEOUT from bounded waits)
+  long long timeout_cycles = 0;
+  int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
   uint64_t* launch_sink = nullptr;  // where enqueue helpers count launches
 };
@@ -94,11 +103,14 @@ size_t bond_bytes(int prec) { return prec == HSG_F16 ? 16 : 24; }
 
 void free_ctx(hsg_ctx* h) {
   if (!h) return;
-  if (h->g_step) cudaGraphExecDestroy(h->g_step);
-  if (h->g_step_m) cudaGraphExecDestroy(h->g_step_m);
+  for (int a = 0; a < 2; ++a)
+    for (int m = 0; m < 2; ++m)
+      if (h->g_step[a][m]) cudaGraphExecDestroy(h->g_step[a][m]);
+  cudaFree(h->d_status);
   for (Bucket& b : h->buckets) {
     cudaFree(b.d_samples);
-    cudaFree(b.d_spins);
+    cudaFree(b.d_spins[0]);
+    cudaFree(b.d_spins[1]);
     cudaFree(b.d_J);
     cudaFree(b.d_epart);
     cudaFree(b.d_mpart);
@@ -138,12 +150,19 @@ hsg_status dalloc(T** p, size_t n) {
 
 int acc_stride(const hsg_ctx* h) { return h->NT > 1 ? h->NT - 1 : 1; }
 
+// Storage position of the natural site i = x + L*(y + L*z) (parity-split rows,
+// as on the device).
+size_t storage_site(size_t i, int L) {
+  const size_t x = i % L, row = i / L;
+  return row * L + (x & 1) * (L / 2) + (x >> 1);
+}
+
 // ----------------------------------------------------------------------------
 // Enqueue helpers (stream-ordered; used directly and under graph capture)
 // ----------------------------------------------------------------------------
 BucketView view(const Bucket& b) {
   BucketView v;
-  v.spins = b.d_spins;
+  v.spins = b.d_spins[b.cur];
   v.J = b.d_J;
   v.sample_ids = b.d_samples;
   v.L = b.L;
@@ -168,14 +187,110 @@ hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cud
   const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.sweep_chunks);
   *h->launch_sink += 1;
   if (h->V == 2) {
-    if (h->prec == HSG_F16) k_sweep_half<KIND, 2, kPrecF16><<<grid, kSweepThreads, 0, st>>>(p);
-    else k_sweep_half<KIND, 2, kPrecF32><<<grid, kSweepThreads, 0, st>>>(p);
+    if (h->prec == HSG_F16) k_sweep_half<KIND, 2, kPrecF16, true><<<grid, kSweepThreads, 0, st>>>(p);
+    else k_sweep_half<KIND, 2, kPrecF32, true><<<grid, kSweepThreads, 0, st>>>(p);
   } else {
-    if (h->prec == HSG_F16) k_sweep_half<KIND, 1, kPrecF16><<<grid, kSweepThreads, 0, st>>>(p);
-    else k_sweep_half<KIND, 1, kPrecF32><<<grid, kSweepThreads, 0, st>>>(p);
+    if (h->prec == HSG_F16) k_sweep_half<KIND, 1, kPrecF16, true><<<grid, kSweepThreads, 0, st>>>(p);
+    else k_sweep_half<KIND, 1, kPrecF32, true><<<grid, kSweepThreads, 0, st>>>(p);
   }
   HSG_CUDA(cudaGetLastError());
   return HSG_OK;
+}
+
+template <int KIND, int V, int PREC>
+void fused_kernel_launch(const FusedParams& p, unsigned grid, unsigned block, size_t smem, cudaStream_t st) {
+  k_sweep_fused<KIND, V, PREC><<<grid, block, smem, st>>>(p);
+}
+
+// One whole sweep (both colours) of a bucket with the fused kernel; reads the
+// current buffer, writes the other, then flips the bucket's buffer index.
+// With probe_timeout the kernel only exercises its bounded-wait failure path
+// (it writes no spins and the buffer index is kept).
+template <int KIND>
+hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, bool probe_timeout = false,
+                        long long timeout = 0) {
+  FusedParams p;
+  p.in = b.d_spins[b.cur];
+  p.out = b.d_spins[b.cur ^ 1];
+  p.J = b.d_J;
+  p.sample_ids = b.d_samples;
+  p.L = b.L;
+  p.N = b.N;
+  p.G = b.G;
+  p.R = h->R;
+  p.band_rows = b.band_rows;
+  p.n_bands = b.n_bands;
+  p.temp_of = h->d_temp_of;
+  p.beta_f = h->d_beta_f;
+  p.key = philox_key(h->seed);
+  p.counters = h->d_counters;
+  p.e_partial = energy ? b.d_epart : nullptr;
+  p.status = h->d_status;
+  p.timeout = timeout > 0 ? timeout : h->timeout_cycles;
+  p.probe_timeout = probe_timeout ? 1 : 0;
+  const int rows_t = (b.band_rows == b.L) ? b.L : b.band_rows + 2;
+  const unsigned block = static_cast<unsigned>(((rows_t * (b.L / 2)) + 31) / 32 * 32);
+  const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.n_bands);
+  *h->launch_sink += 1;
+  if (h->V == 2) {
+    if (h->prec == HSG_F16) fused_kernel_launch<KIND, 2, kPrecF16>(p, grid, block, b.fused_smem, st);
+    else fused_kernel_launch<KIND, 2, kPrecF32>(p, grid, block, b.fused_smem, st);
+  } else {
+    if (h->prec == HSG_F16) fused_kernel_launch<KIND, 1, kPrecF16>(p, grid, block, b.fused_smem, st);
+    else fused_kernel_launch<KIND, 1, kPrecF32>(p, grid, block, b.fused_smem, st);
+  }
+  HSG_CUDA(cudaGetLastError());
+  if (!probe_timeout) b.cur ^= 1;
+  return HSG_OK;
+}
+
+template <int KIND, int V, int PREC>
+hsg_status allow_fused_smem(size_t bytes) {
+  HSG_CUDA(cudaFuncSetAttribute(k_sweep_fused<KIND, V, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(bytes)));
+  return HSG_OK;
+}
+
+hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
+  if (V == 2 && prec == HSG_F16) {
+    HSG_TRY((allow_fused_smem<kHB, 2, kPrecF16>(bytes)));
+    return allow_fused_smem<kOR, 2, kPrecF16>(bytes);
+  }
+  if (V == 2) {
+    HSG_TRY((allow_fused_smem<kHB, 2, kPrecF32>(bytes)));
+    return allow_fused_smem<kOR, 2, kPrecF32>(bytes);
+  }
+  if (prec == HSG_F16) {
+    HSG_TRY((allow_fused_smem<kHB, 1, kPrecF16>(bytes)));
+    return allow_fused_smem<kOR, 1, kPrecF16>(bytes);
+  }
+  HSG_TRY((allow_fused_smem<kHB, 1, kPrecF32>(bytes)));
+  return allow_fused_smem<kOR, 1, kPrecF32>(bytes);
+}
+
+// Tiling of the fused sweep for lattice size L and V lattices per element:
+// whole planes if they fit, else the widest band of rows (a divisor of L, at
+// least 8) within the thread and shared-memory limits.  False: use the
+// two-pass half-sweep kernel.
+bool plan_fused(int L, int V, int* band_rows, size_t* smem) {
+  const size_t max_smem = 200 * 1024;
+  auto smem_for = [&](int rows) { return static_cast<size_t>(kFusedSlots) * 3 * rows * L * V * sizeof(float); };
+  auto threads_for = [&](int rows) { return rows * (L / 2); };
+  if (threads_for(L) <= kFusedMaxThreads && smem_for(L) <= max_smem) {
+    *band_rows = L;
+    *smem = smem_for(L);
+    return true;
+  }
+  if ((L * V) % 4 != 0) return false;  // 16-byte rows for the bulk copies
+  for (int B = L / 2; B >= 8; --B) {
+    if (L % B != 0) continue;
+    if (threads_for(B + 2) <= kFusedMaxThreads && smem_for(B + 4) <= max_smem) {
+      *band_rows = B;
+      *smem = smem_for(B + 4);
+      return true;
+    }
+  }
+  return false;
 }
 
 hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st) {
@@ -186,18 +301,27 @@ hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st)
 }
 
 hsg_status enqueue_hb_sweep(hsg_ctx* h, cudaStream_t st) {
-  for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kHB>(h, b, 0, false, st));
-  for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kHB>(h, b, 1, false, st));
+  for (Bucket& b : h->buckets) {
+    if (b.fused) {
+      HSG_TRY(launch_fused<kHB>(h, b, false, st));
+    } else {
+      HSG_TRY(launch_half<kHB>(h, b, 0, false, st));
+      HSG_TRY(launch_half<kHB>(h, b, 1, false, st));
+    }
+  }
   return HSG_OK;
 }
 
-hsg_status enqueue_energy_finalize(hsg_ctx* h, cudaStream_t st) {
+// E = sum of each lattice's partials; `from_sweep` selects the partial layout
+// of the sweep kernels (fused: one per band) over that of the energy pass.
+hsg_status enqueue_energy_finalize(hsg_ctx* h, bool from_sweep, cudaStream_t st) {
   for (const Bucket& b : h->buckets) {
     const int n_lat = b.S_b * h->R;
     const int threads = 256;
     const int blocks = (n_lat * 32 + threads - 1) / threads;
+    const int chunks = (from_sweep && b.fused) ? b.n_bands : b.sweep_chunks;
     *h->launch_sink += 1;
-    k_energy_finalize<<<blocks, threads, 0, st>>>(b.d_epart, b.sweep_chunks, n_lat, b.d_samples, h->R, h->d_E);
+    k_energy_finalize<<<blocks, threads, 0, st>>>(b.d_epart, chunks, n_lat, b.d_samples, h->R, h->d_E);
     HSG_CUDA(cudaGetLastError());
   }
   return HSG_OK;
@@ -207,16 +331,22 @@ hsg_status enqueue_energy_finalize(hsg_ctx* h, cudaStream_t st) {
 hsg_status enqueue_or_sweeps(hsg_ctx* h, int n, cudaStream_t st) {
   for (int s = 0; s < n; ++s) {
     const bool last = (s == n - 1);
-    for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kOR>(h, b, 0, false, st));
-    for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kOR>(h, b, 1, last, st));
+    for (Bucket& b : h->buckets) {
+      if (b.fused) {
+        HSG_TRY(launch_fused<kOR>(h, b, last, st));
+      } else {
+        HSG_TRY(launch_half<kOR>(h, b, 0, false, st));
+        HSG_TRY(launch_half<kOR>(h, b, 1, last, st));
+      }
+    }
   }
-  if (n > 0) HSG_TRY(enqueue_energy_finalize(h, st));
+  if (n > 0) HSG_TRY(enqueue_energy_finalize(h, true, st));
   return HSG_OK;
 }
 
 hsg_status enqueue_energy(hsg_ctx* h, cudaStream_t st) {
   for (const Bucket& b : h->buckets) HSG_TRY(launch_half<kEnergyOnly>(h, b, 1, true, st));
-  return enqueue_energy_finalize(h, st);
+  return enqueue_energy_finalize(h, false, st);
 }
 
 hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st) {
@@ -274,14 +404,30 @@ hsg_status enqueue_step(hsg_ctx* h, bool with_measure, cudaStream_t st) {
   return enqueue_bump(h, 1, 1, st);
 }
 
-hsg_status capture_graph(hsg_ctx* h, bool with_measure, cudaGraphExec_t* out, uint64_t* n_kernels) {
+// Buffer index of the buckets swept by the fused kernel (they all flip
+// together, so one parity describes them); 0 if there are none.
+int fused_parity(const hsg_ctx* h) {
+  for (const Bucket& b : h->buckets)
+    if (b.fused) return b.cur;
+  return 0;
+}
+
+// Captures one step starting from fused-buffer parity `par`; the buckets'
+// buffer indices are left as they were.
+hsg_status capture_graph(hsg_ctx* h, int par, bool with_measure, cudaGraphExec_t* out, uint64_t* n_kernels) {
   cudaGraph_t graph = nullptr;
+  std::vector<int> saved;
+  for (Bucket& b : h->buckets) {
+    saved.push_back(b.cur);
+    if (b.fused) b.cur = par;
+  }
   HSG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   *n_kernels = 0;
   h->launch_sink = n_kernels;
   hsg_status st = enqueue_step(h, with_measure, h->cap_stream);
   h->launch_sink = &h->launches;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  for (size_t j = 0; j < h->buckets.size(); ++j) h->buckets[j].cur = saved[j];
   if (st != HSG_OK) {
     if (graph) cudaGraphDestroy(graph);
     return st;
@@ -290,6 +436,18 @@ hsg_status capture_graph(hsg_ctx* h, bool with_measure, cudaGraphExec_t* out, ui
   e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(HSG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  return HSG_OK;
+}
+
+// HSG_ETIMEOUT if a kernel recorded an expired bounded wait since the last
+// check (the word is then cleared); call after synchronising the stream.
+hsg_status status_check(hsg_ctx* h) {
+  int st = 0;
+  HSG_CUDA(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    HSG_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    return fail(HSG_ETIMEOUT, "a device-side wait gave up (timeout_cycles exceeded); that launch did not complete");
+  }
   return HSG_OK;
 }
 
@@ -321,6 +479,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   if (cfg->layout != HSG_LAYOUT_PLAIN && cfg->layout != HSG_LAYOUT_BATCHED)
     return fail(HSG_EINVAL, "layout must be HSG_LAYOUT_PLAIN or HSG_LAYOUT_BATCHED");
   if (cfg->n_or < 0 || cfg->measure_every < 0) return fail(HSG_EINVAL, "n_or and measure_every must be >= 0");
+  if (cfg->sweep_kernel != HSG_SWEEP_AUTO && cfg->sweep_kernel != HSG_SWEEP_TWO_PASS)
+    return fail(HSG_EINVAL, "sweep_kernel must be HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS");
   for (int s = 0; s < cfg->n_samples; ++s) {
     const int L = cfg->L[s];
     if (L < 4 || L > 512 || (L & 1)) return fail(HSG_EINVAL, "each L must be even and in [4, 512]");
@@ -348,6 +508,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   h->measure_every = cfg->measure_every;
   h->seed = cfg->seed;
   h->stream = static_cast<cudaStream_t>(cfg->stream);
+  h->timeout_cycles = cfg->timeout_cycles > 0 ? cfg->timeout_cycles : 4000000000LL;
+  h->sweep_kernel = cfg->sweep_kernel;
   h->launch_sink = &h->launches;
   h->Ls.assign(cfg->L, cfg->L + cfg->n_samples);
   h->beta.assign(cfg->beta, cfg->beta + cfg->n_temps);
@@ -388,6 +550,9 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     b.S_b = static_cast<int>(b.samples.size());
     b.G = h->R / V;
     b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
+    b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) && plan_fused(b.L, V, &b.band_rows, &b.fused_smem);
+    b.n_bands = b.fused ? b.L / b.band_rows : 0;
+    if (b.fused && allow_fused_smem_all(V, h->prec, b.fused_smem) != HSG_OK) return bail(HSG_ECUDA);
     b.P = (h->n_rep + 1) / 2;
     const int units = b.S_b * h->NT * b.P;
     const int by_size = std::max(1, b.N / (kMeasureThreads * 16));
@@ -397,10 +562,12 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     const size_t n_spin = static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
     hsg_status st;
     if ((st = dalloc(&b.d_samples, b.S_b)) != HSG_OK) return bail(st);
-    if ((st = dalloc(&b.d_spins, n_spin)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_spins[0], n_spin)) != HSG_OK) return bail(st);
+    if (b.fused && (st = dalloc(&b.d_spins[1], n_spin)) != HSG_OK) return bail(st);
     const size_t jbytes = static_cast<size_t>(b.S_b) * 3 * b.N * bond_bytes(h->prec);
     if ((st = dalloc(reinterpret_cast<char**>(&b.d_J), jbytes)) != HSG_OK) return bail(st);
-    if ((st = dalloc(&b.d_epart, static_cast<size_t>(b.S_b) * h->R * b.sweep_chunks)) != HSG_OK) return bail(st);
+    if ((st = dalloc(&b.d_epart, static_cast<size_t>(b.S_b) * h->R * std::max(b.sweep_chunks, b.n_bands))) != HSG_OK)
+      return bail(st);
     if ((st = dalloc(&b.d_mpart, static_cast<size_t>(units) * b.m_chunks * kNQ)) != HSG_OK) return bail(st);
     if ((st = dalloc(&b.d_phase, 2 * static_cast<size_t>(b.L))) != HSG_OK) return bail(st);
     if (cudaMemcpy(b.d_samples, b.samples.data(), sizeof(int) * b.S_b, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -421,7 +588,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
       return bail(HSG_ECUDA);
     }
     const size_t per_block = static_cast<size_t>(b.N) * V;
-    k_fill_spins<<<static_cast<unsigned>((n_spin + 255) / 256), 256>>>(b.d_spins, per_block, n_spin);
+    k_fill_spins<<<static_cast<unsigned>((n_spin + 255) / 256), 256>>>(b.d_spins[0], per_block, n_spin);
   }
 
   const size_t S = h->S, NT = h->NT;
@@ -435,6 +602,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   if ((st = dalloc(&h->d_counts, S * NT)) != HSG_OK) return bail(st);
   if ((st = dalloc(&h->d_pt_acc, S * h->n_rep * acc_stride(h))) != HSG_OK) return bail(st);
   if ((st = dalloc(&h->d_counters, 2)) != HSG_OK) return bail(st);
+  if ((st = dalloc(&h->d_status, 1)) != HSG_OK) return bail(st);
   if ((st = dalloc(&h->d_stage, 3 * max_N)) != HSG_OK) return bail(st);
 
   std::vector<int> perm(S * h->n_rep * NT), temp_of(S * h->R);
@@ -456,6 +624,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
       cudaMemset(h->d_counts, 0, sizeof(long long) * S * NT) != cudaSuccess ||
       cudaMemset(h->d_pt_acc, 0, sizeof(long long) * S * h->n_rep * acc_stride(h)) != cudaSuccess ||
       cudaMemset(h->d_counters, 0, sizeof(uint32_t) * 2) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     cudaError_t e = cudaGetLastError();
     fail(HSG_ECUDA, std::string("initialising context buffers failed: ") + cudaGetErrorString(e));
@@ -474,7 +643,20 @@ void hsg_destroy(hsg_t h) {
 hsg_status hsg_synchronize(hsg_t h) {
   if (!h) return fail(HSG_EINVAL, "handle is NULL");
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  return HSG_OK;
+  return status_check(h);
+}
+
+hsg_status hsg_selftest_wait_timeout(hsg_t h, long long timeout_cycles) {
+  if (!h || timeout_cycles <= 0) return fail(HSG_EINVAL, "bad handle or timeout_cycles <= 0");
+  Bucket* fb = nullptr;
+  for (Bucket& b : h->buckets)
+    if (b.fused) fb = &b;
+  if (!fb) return fail(HSG_ESTATE, "no bucket uses the fused sweep, which holds the bounded waits");
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_TRY(status_check(h));
+  HSG_TRY(launch_fused<kOR>(h, *fb, false, h->stream, true, timeout_cycles));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return status_check(h);
 }
 
 hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
@@ -489,14 +671,15 @@ hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
     float* out = reinterpret_cast<float*>(buf.data());
     for (size_t i = 0; i < N; ++i)
       for (int mu = 0; mu < 3; ++mu)
-        for (int e = 0; e < 6; ++e) out[(mu * N + i) * 6 + e] = J6[(i * 3 + mu) * 6 + e];
+        for (int e = 0; e < 6; ++e) out[(mu * N + storage_site(i, b.L)) * 6 + e] = J6[(i * 3 + mu) * 6 + e];
   } else {
     __half* out = reinterpret_cast<__half*>(buf.data());
     for (size_t i = 0; i < N; ++i)
       for (int mu = 0; mu < 3; ++mu) {
-        for (int e = 0; e < 6; ++e) out[(mu * N + i) * 8 + e] = __float2half_rn(J6[(i * 3 + mu) * 6 + e]);
-        out[(mu * N + i) * 8 + 6] = __float2half_rn(0.0f);
-        out[(mu * N + i) * 8 + 7] = __float2half_rn(0.0f);
+        const size_t d = mu * N + storage_site(i, b.L);
+        for (int e = 0; e < 6; ++e) out[d * 8 + e] = __float2half_rn(J6[(i * 3 + mu) * 6 + e]);
+        out[d * 8 + 6] = __float2half_rn(0.0f);
+        out[d * 8 + 7] = __float2half_rn(0.0f);
       }
   }
   HSG_CUDA(cudaStreamSynchronize(h->stream));
@@ -521,8 +704,9 @@ hsg_status hsg_get_couplings(hsg_t h, int sample, float* J6) {
     for (int mu = 0; mu < 3; ++mu)
       for (int e = 0; e < 6; ++e) {
         float v;
-        if (h->prec == HSG_F32) v = reinterpret_cast<const float*>(buf.data())[(mu * N + i) * 6 + e];
-        else v = __half2float(reinterpret_cast<const __half*>(buf.data())[(mu * N + i) * 8 + e]);
+        const size_t d = mu * N + storage_site(i, b.L);
+        if (h->prec == HSG_F32) v = reinterpret_cast<const float*>(buf.data())[d * 6 + e];
+        else v = __half2float(reinterpret_cast<const __half*>(buf.data())[d * 8 + e]);
         J6[(i * 3 + mu) * 6 + e] = v;
       }
   return HSG_OK;
@@ -540,9 +724,9 @@ hsg_status hsg_set_spins(hsg_t h, int sample, int slot, const float* s) {
   if (!s) return fail(HSG_EINVAL, "spins pointer is NULL");
   Bucket& b = h->buckets[h->sample_bucket[sample]];
   const int sb = h->sample_local[sample];
-  float* base = b.d_spins + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  float* base = b.d_spins[b.cur] + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
   HSG_CUDA(cudaMemcpyAsync(h->d_stage, s, sizeof(float) * 3 * b.N, cudaMemcpyHostToDevice, h->stream));
-  k_scatter_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(h->d_stage, base, b.N, h->V, slot % h->V);
+  k_scatter_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(h->d_stage, base, b.L, h->V, slot % h->V);
   HSG_CUDA(cudaGetLastError());
   HSG_CUDA(cudaStreamSynchronize(h->stream));
   h->energy_valid = false;
@@ -554,12 +738,13 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float* s_out) {
   if (!s_out) return fail(HSG_EINVAL, "output pointer is NULL");
   Bucket& b = h->buckets[h->sample_bucket[sample]];
   const int sb = h->sample_local[sample];
-  const float* base = b.d_spins + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
-  k_gather_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(base, h->d_stage, b.N, h->V, slot % h->V);
+  const float* base =
+      b.d_spins[b.cur] + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  k_gather_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(base, h->d_stage, b.L, h->V, slot % h->V);
   HSG_CUDA(cudaGetLastError());
   HSG_CUDA(cudaMemcpyAsync(s_out, h->d_stage, sizeof(float) * 3 * b.N, cudaMemcpyDeviceToHost, h->stream));
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  return HSG_OK;
+  return status_check(h);
 }
 
 hsg_status hsg_sweep_hb(hsg_t h, int n) {
@@ -593,7 +778,7 @@ hsg_status hsg_get_energies(hsg_t h, double* E_out) {
   if (!h->energy_valid) HSG_TRY(hsg_energy(h));
   HSG_CUDA(cudaMemcpyAsync(E_out, h->d_E, sizeof(double) * h->S * h->R, cudaMemcpyDeviceToHost, h->stream));
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  return HSG_OK;
+  return status_check(h);
 }
 
 hsg_status hsg_set_energies(hsg_t h, const double* E) {
@@ -659,13 +844,18 @@ hsg_status hsg_measure(hsg_t h) {
 hsg_status hsg_run_steps(hsg_t h, int n_steps) {
   if (!h || n_steps < 0) return fail(HSG_EINVAL, "bad handle or n_steps < 0");
   if (n_steps == 0) return HSG_OK;
-  if (!h->g_step) HSG_TRY(capture_graph(h, false, &h->g_step, &h->g_step_launches));
-  if (h->measure_every > 0 && !h->g_step_m) HSG_TRY(capture_graph(h, true, &h->g_step_m, &h->g_step_m_launches));
+  // sweeps per step: one heat-bath sweep plus n_or overrelaxation sweeps;
+  // each fused sweep flips the buffer index
+  const int flips = (1 + h->n_or) & 1;
   for (int s = 0; s < n_steps; ++s) {
     const uint64_t next = h->counters[2] + 1;
-    const bool m = h->measure_every > 0 && (next % static_cast<uint64_t>(h->measure_every)) == 0;
-    HSG_CUDA(cudaGraphLaunch(m ? h->g_step_m : h->g_step, h->stream));
-    h->launches += m ? h->g_step_m_launches : h->g_step_launches;
+    const int m = (h->measure_every > 0 && (next % static_cast<uint64_t>(h->measure_every)) == 0) ? 1 : 0;
+    const int par = fused_parity(h);
+    if (!h->g_step[par][m]) HSG_TRY(capture_graph(h, par, m != 0, &h->g_step[par][m], &h->g_step_launches[par][m]));
+    HSG_CUDA(cudaGraphLaunch(h->g_step[par][m], h->stream));
+    h->launches += h->g_step_launches[par][m];
+    for (Bucket& b : h->buckets)
+      if (b.fused) b.cur ^= flips;
     h->counters[0] += 1;
     h->counters[1] += 1;
     h->counters[2] = next;
@@ -681,7 +871,7 @@ hsg_status hsg_read_observables(hsg_t h, double* obs_out, long long* counts_out)
   if (counts_out)
     HSG_CUDA(cudaMemcpyAsync(counts_out, h->d_counts, sizeof(long long) * n, cudaMemcpyDeviceToHost, h->stream));
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  return HSG_OK;
+  return status_check(h);
 }
 
 hsg_status hsg_reset_observables(hsg_t h) {
@@ -736,7 +926,7 @@ struct DevArray {
 std::vector<DevArray> checkpoint_arrays(hsg_ctx* h) {
   std::vector<DevArray> a;
   for (Bucket& b : h->buckets) {
-    a.push_back({b.d_spins, sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N});
+    a.push_back({b.d_spins[b.cur], sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N});
     a.push_back({b.d_J, static_cast<size_t>(b.S_b) * 3 * b.N * bond_bytes(h->prec)});
   }
   const size_t S = h->S, NT = h->NT;

@@ -4,9 +4,13 @@
 // Device layout of one bucket (samples of equal L; N = L^3 sites, V lattices
 // interleaved per element, G = R/V lattice groups per sample):
 //   spins   float [S_b][G][3][N][V]   component planes, lattice lane innermost
-//   J f32   float [S_b][3][N][6]      bond (i, i+e_mu) at [mu][i]: xx,yy,zz,xy,xz,yz
+//   J f32   float [S_b][3][N][6]      bond (x, x+e_mu) at [mu][site]: xx,yy,zz,xy,xz,yz
 //   J f16   half  [S_b][3][N][8]      same six entries + two zero pads (16 B/bond)
-// Site i = x + L*(y + L*z); black sites have x+y+z even.
+// Storage order of the sites ("parity-split rows"): row = y + L*z, and within
+// a row the L/2 sites of even x come first, then the L/2 sites of odd x:
+//   site(x, y, z) = (y + L*z)*L + (x & 1)*(L/2) + (x >> 1).
+// Black sites have x+y+z even.  Random-number counters always use the
+// natural index x + L*(y + L*z), so they do not depend on the storage order.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -162,6 +166,14 @@ __device__ __forceinline__ void overrelax(float hx, float hy, float hz, float& s
   }
 }
 
+// Storage index of site (x, row) with row = y + L*z: parity-split when SPLIT,
+// natural order x + L*row otherwise.
+template <bool SPLIT>
+__device__ __forceinline__ int site_of(int x, int row, int L) {
+  if constexpr (SPLIT) return row * L + (x & 1) * (L >> 1) + (x >> 1);
+  return row * L + x;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -176,7 +188,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // lattice energy, since every bond has exactly one white end and
 // overrelaxation keeps s.h.
 // ---------------------------------------------------------------------------
-template <int KIND, int V, int PREC>
+template <int KIND, int V, int PREC, bool SPLIT = false>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
   const BucketView& b = p.b;
   const int gi = blockIdx.x / p.chunks;  // lattice group within the bucket
@@ -195,10 +207,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
     const int y = row % L;
     const int z = row / L;
     const int x = 2 * k + ((p.colour + y + z) & 1);
-    const int i = x + L * row;
+    const int i_nat = x + L * row;
+    const int i = site_of<SPLIT>(x, row, L);
     const int LL = L * L;
-    const int ixm = (x == 0) ? i + (L - 1) : i - 1;
-    const int ixp = (x == L - 1) ? i - (L - 1) : i + 1;
+    const int ixm = site_of<SPLIT>((x == 0) ? L - 1 : x - 1, row, L);
+    const int ixp = site_of<SPLIT>((x == L - 1) ? 0 : x + 1, row, L);
     const int iym = (y == 0) ? i + (L - 1) * L : i - L;
     const int iyp = (y == L - 1) ? i - (L - 1) * L : i + L;
     const int izm = (z == 0) ? i + (L - 1) * LL : i - LL;
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
       const uint32_t t = p.counters[0];
       const int sg = b.sample_ids[sb];
       const uint32_t lat0 = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(g * V);
-      const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i), lat0 >> 1, t, kTagHeatBath), p.key);
+      const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i_nat), lat0 >> 1, t, kTagHeatBath), p.key);
       float out[3][V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -395,9 +408,13 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
   const int end = min(N, start + per_chunk);
   int batch = 0;
   for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
-    const int x = i % L, y = (i / L) % L, z = i / (L * L);
+    const int row = i / L, jr = i - row * L;
+    const int half = L >> 1;
+    const int x = (jr < half) ? 2 * jr : 2 * (jr - half) + 1;
+    const int y = row % L, z = row / L;
     const int LL = L * L;
-    const int nb[6] = {(x == L - 1) ? i - (L - 1) : i + 1, (x == 0) ? i + (L - 1) : i - 1,
+    const int nb[6] = {site_of<true>((x == L - 1) ? 0 : x + 1, row, L),
+                       site_of<true>((x == 0) ? L - 1 : x - 1, row, L),
                        (y == L - 1) ? i - (L - 1) * L : i + L, (y == 0) ? i + (L - 1) * L : i - L,
                        (z == L - 1) ? i - (L - 1) * LL : i + LL, (z == 0) ? i + (L - 1) * LL : i - LL};
     float sa[3], sbv[3];
@@ -533,19 +550,24 @@ static __global__ void k_measure_finalize(const double* __restrict__ partial, co
   counts[static_cast<size_t>(sg) * NT + k] += 1;
 }
 
-// Host spins [N][3] (staged on the device) <-> one lane of the device layout.
-static __global__ void k_scatter_spins(const float* __restrict__ stage, float* __restrict__ base, int N, int V, int v) {
+// Host spins [N][3] in natural site order (staged on the device) <-> one lane
+// of the device layout (parity-split storage order).
+static __global__ void k_scatter_spins(const float* __restrict__ stage, float* __restrict__ base, int L, int V, int v) {
+  const int N = L * L * L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int d = site_of<true>(i % L, i / L, L);
   const size_t plane = static_cast<size_t>(N) * V;
-  for (int c = 0; c < 3; ++c) base[c * plane + static_cast<size_t>(i) * V + v] = stage[3 * static_cast<size_t>(i) + c];
+  for (int c = 0; c < 3; ++c) base[c * plane + static_cast<size_t>(d) * V + v] = stage[3 * static_cast<size_t>(i) + c];
 }
 
-static __global__ void k_gather_spins(const float* __restrict__ base, float* __restrict__ stage, int N, int V, int v) {
+static __global__ void k_gather_spins(const float* __restrict__ base, float* __restrict__ stage, int L, int V, int v) {
+  const int N = L * L * L;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int d = site_of<true>(i % L, i / L, L);
   const size_t plane = static_cast<size_t>(N) * V;
-  for (int c = 0; c < 3; ++c) stage[3 * static_cast<size_t>(i) + c] = base[c * plane + static_cast<size_t>(i) * V + v];
+  for (int c = 0; c < 3; ++c) stage[3 * static_cast<size_t>(i) + c] = base[c * plane + static_cast<size_t>(d) * V + v];
 }
 
 static __global__ void k_fill_spins(float* __restrict__ spins, size_t n_per_comp_block, size_t total) {

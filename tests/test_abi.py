@@ -50,6 +50,7 @@ def _cfg(**kw):
     c.seed = 1
     c.stream = None
     c.timeout_cycles = 0
+    c.sweep_kernel = kw.pop("sweep_kernel", 0)
     return c, (L, beta)
 
 
@@ -59,6 +60,7 @@ def _cfg(**kw):
     (dict(prec=5), "coupling_prec"), (dict(layout=9), "layout"),
     (dict(layout=1, n_replicas=1, beta=[1.0]), "even number"),
     (dict(n_replicas=0), "n_replicas"),
+    (dict(sweep_kernel=7), "sweep_kernel"),
 ])
 def test_invalid_configs_rejected_on_host(lib, kw, msg):
     c, keep = _cfg(**kw)
