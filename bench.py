@@ -43,6 +43,9 @@ WORKLOADS = {
     # profiling size: 512 lattices of L=32 (201 MB of spins, above L2)
     "L32_S8_R64_f16": dict(L=32, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
+    # profiling size of the L=64 tiling: one sample, 64 lattices (201 MB of spins)
+    "L64_S1_R64_f16": dict(L=64, S=1, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
+                           measure_every=10),
 }
 DEFAULT_WORKLOAD = "L64_S8_R64_f16"
 
@@ -53,7 +56,7 @@ NCU_TRAFFIC = {}
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "philox.cuh", "hsg.cu"):
+    for f in ("kernels.cuh", "fused.cuh", "philox.cuh", "hsg.cu"):
         with open(os.path.join(ROOT, "paper_1309_1599_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -212,8 +215,9 @@ def time_steps(lat, steps, torch, dist, sampler=None):
 
 
 def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
-    """Average duration of one overrelaxation half-sweep launch (the dominant
-    kernel), from CUDA events around sweep_or calls on the library's stream."""
+    """Average duration of one overrelaxation sweep-kernel launch (the
+    dominant kernel: one fused sweep, or one colour half-sweep), from CUDA
+    events around sweep_or calls on the library's stream."""
     stream = torch.cuda.current_stream()
     lat.sweep_or(sweeps)
     torch.cuda.synchronize()
@@ -224,7 +228,8 @@ def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
         lat.sweep_or(sweeps)
     e1.record(stream)
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / (n_calls * 2 * sweeps)
+    per_sweep = lat.get_sweep_plan(0)["launches_per_sweep"]
+    return e0.elapsed_time(e1) / (n_calls * per_sweep * sweeps)
 
 
 def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak):
@@ -242,10 +247,16 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
     bond_bytes = 12 if prec == hsg.F16 else 24
     r_share = R if layout == hsg.BATCHED else 1
     balg = b_alg(r_share, bond_bytes)
-    bytes_launch = S * R * (N // 2) * balg
+    plan = lat.get_sweep_plan(0)
+    # updates per launch: every site (fused sweep) or half of them (half-sweep)
+    upd_launch = S * R * N // plan["launches_per_sweep"]
+    bytes_launch = upd_launch * balg
     achieved = bytes_launch / (or_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": f"k_sweep_half<OR,{2 if layout == hsg.BATCHED else 1},"
-                                      f"{'f16' if prec == hsg.F16 else 'f32'}>",
+    vname = 2 if layout == hsg.BATCHED else 1
+    pname = "f16" if prec == hsg.F16 else "f32"
+    kname = (f"k_sweep_fused<OR,{vname},{pname}> (bands of {plan['band_rows']} rows)" if plan["fused"]
+             else f"k_sweep_half<OR,{vname},{pname}>")
+    roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peak[0], "peak_source": peak[1],
             "unit": "GB/s", "frac": round(achieved / peak[0], 4),
             "b_alg_bytes_per_update": round(balg, 4),

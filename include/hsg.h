@@ -185,6 +185,11 @@ hsg_status hsg_reset_observables(hsg_t h);
 hsg_status hsg_get_counters(hsg_t h, uint64_t out[3]);
 hsg_status hsg_set_counters(hsg_t h, const uint64_t in[3]);
 
+/* How the sweeps of `sample` run: out[0] = 1 for the fused one-pass kernel,
+ * 0 for two half-sweep kernels; out[1] = rows per band of the fused kernel
+ * (L for whole planes); out[2] = kernel launches per sweep. */
+hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]);
+
 /* Number of compute kernels this context has enqueued so far (sweeps,
  * energies, PT, measurement and counter updates, including those replayed
  * from graphs; data-transfer helpers are not counted). */

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "hsg_get_counters": [ctypes.c_void_p, ctypes.c_void_p],
     "hsg_set_counters": [ctypes.c_void_p, ctypes.c_void_p],
     "hsg_get_launch_count": [ctypes.c_void_p, ctypes.c_void_p],
+    "hsg_get_sweep_plan": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_save": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_load": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_synchronize": [ctypes.c_void_p],
@@ -283,6 +284,11 @@ class Lattice:
     def set_counters(self, hb: int, pt: int, steps: int) -> None:
         a = np.array([hb, pt, steps], dtype=np.uint64)
         _check(self._lib.hsg_set_counters(self._h, _ptr(a)))
+
+    def get_sweep_plan(self, sample: int = 0) -> dict:
+        out = np.zeros(3, dtype=np.int32)
+        _check(self._lib.hsg_get_sweep_plan(self._h, sample, _ptr(out)))
+        return {"fused": bool(out[0]), "band_rows": int(out[1]), "launches_per_sweep": int(out[2])}
 
     def get_launch_count(self) -> int:
         out = np.zeros(1, dtype=np.uint64)

@@ -544,7 +544,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     return bail(HSG_ECUDA);
   }
 
-  size_t max_N = 0;
+  size_t max_N = 0, max_fused_smem = 0;
   for (Bucket& b : h->buckets) {
     b.N = b.L * b.L * b.L;
     b.S_b = static_cast<int>(b.samples.size());
@@ -552,7 +552,9 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
     b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) && plan_fused(b.L, V, &b.band_rows, &b.fused_smem);
     b.n_bands = b.fused ? b.L / b.band_rows : 0;
-    if (b.fused && allow_fused_smem_all(V, h->prec, b.fused_smem) != HSG_OK) return bail(HSG_ECUDA);
+    // the shared-memory limit is a property of the kernel, not of the bucket:
+    // raise it to what the largest tiling in this context needs
+    if (b.fused) max_fused_smem = std::max(max_fused_smem, b.fused_smem);
     b.P = (h->n_rep + 1) / 2;
     const int units = b.S_b * h->NT * b.P;
     const int by_size = std::max(1, b.N / (kMeasureThreads * 16));
@@ -591,6 +593,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     k_fill_spins<<<static_cast<unsigned>((n_spin + 255) / 256), 256>>>(b.d_spins[0], per_block, n_spin);
   }
 
+  if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
   const size_t S = h->S, NT = h->NT;
   hsg_status st;
   if ((st = dalloc(&h->d_perm, S * h->n_rep * NT)) != HSG_OK) return bail(st);
@@ -886,6 +889,16 @@ hsg_status hsg_reset_observables(hsg_t h) {
 hsg_status hsg_get_counters(hsg_t h, uint64_t out[3]) {
   if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
   for (int j = 0; j < 3; ++j) out[j] = h->counters[j];
+  return HSG_OK;
+}
+
+hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]) {
+  if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  const Bucket& b = h->buckets[h->sample_bucket[sample]];
+  out[0] = b.fused ? 1 : 0;
+  out[1] = b.fused ? b.band_rows : 0;
+  out[2] = b.fused ? 1 : 2;
   return HSG_OK;
 }
 

@@ -47,6 +47,7 @@ CASES = [
     ([6], [0.0, 1.0, 5.0], 3, hsg.F16, hsg.PLAIN),         # beta = 0, odd replicas
     ([4], [1.3], 1, hsg.F32, hsg.PLAIN),                   # smallest lattice
     ([16], [1.0, 6.0], 2, hsg.F16, hsg.PLAIN),
+    ([40], [1.2, 3.0], 2, hsg.F16, hsg.BATCHED),          # fused sweep in bands of rows
 ]
 
 
@@ -247,3 +248,55 @@ def test_or_conserves_energy_and_norm_on_gpu():
     for slot in range(lat.R):
         n = np.linalg.norm(lat.get_spins(0, slot), axis=1)
         assert np.abs(n - 1).max() < 1e-4
+
+
+FUSED_CASES = [
+    # (Ls, n_rep, prec, layout): whole-plane and banded tilings of the fused sweep
+    ([8, 12], 2, hsg.F32, hsg.PLAIN),
+    ([16], 2, hsg.F16, hsg.BATCHED),
+    ([32], 1, hsg.F16, hsg.BATCHED),
+    ([40], 1, hsg.F16, hsg.BATCHED),
+    ([48], 1, hsg.F32, hsg.PLAIN),
+]
+
+
+@pytest.mark.parametrize("case", range(len(FUSED_CASES)))
+def test_fused_sweep_equals_two_pass_bitwise(case):
+    """The fused one-pass sweep and the two-pass half-sweeps sum each field in
+    the same order, so they must give identical spins, energies and labels."""
+    Ls, n_rep, prec, layout = FUSED_CASES[case]
+    betas = gi.linear_betas(0.4, 1.2, 2)
+    runs = []
+    for kernel in (hsg.SWEEP_AUTO, hsg.SWEEP_TWO_PASS):
+        lat = hsg.Lattice(Ls, betas, n_replicas=n_rep, coupling_prec=prec, layout=layout, n_or=3,
+                          measure_every=2, seed=5, sweep_kernel=kernel)
+        pstr = "f16" if prec == hsg.F16 else "f32"
+        for s, L in enumerate(Ls):
+            lat.set_couplings(s, gi.couplings(L, 5, s, precision=pstr))
+            for j in range(lat.R):
+                lat.set_spins(s, j, gi.random_spins(L, 5, s, j))
+        lat.sweep_hb(1)
+        lat.sweep_or(2)
+        E1 = lat.get_energies()
+        lat.run_steps(3)
+        runs.append((state(lat), E1, lat.get_energies(), lat.get_perm(), lat.read_observables()[0]))
+        lat.destroy()
+    (sa, e1a, e2a, pa, oa), (sb, e1b, e2b, pb, ob) = runs
+    assert all(np.array_equal(x, y) for rx, ry in zip(sa, sb) for x, y in zip(rx, ry))
+    assert np.allclose(e1a, e1b, rtol=1e-12) and np.allclose(e2a, e2b, rtol=1e-12)
+    assert np.array_equal(pa, pb)
+    assert np.allclose(oa, ob, rtol=1e-9, atol=1e-12)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A device-side wait that runs out is reported as HSG_ETIMEOUT on the
+    host; nothing hangs and the context keeps working."""
+    lat, J = make([8], [2.0], n_rep=2, layout=hsg.BATCHED)
+    before = state(lat)
+    assert lat.selftest_wait_timeout(100000) == 4          # HSG_ETIMEOUT
+    assert all(np.array_equal(x, y) for rx, ry in zip(before, state(lat)) for x, y in zip(rx, ry))
+    hb_t = int(lat.get_counters()[0])
+    lat.sweep_hb(1)
+    lat.synchronize()
+    d, _, _ = compare_sweep(lat, J, before, state(lat), oracle.HB, hb_t)
+    assert d <= SWEEP_TOL
