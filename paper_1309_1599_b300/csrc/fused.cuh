@@ -33,7 +33,7 @@
 
 namespace hsg {
 
-constexpr int kFusedMaxThreads = 640;
+constexpr int kFusedMaxThreads = 576;
 constexpr int kFusedSlots = 4;
 constexpr int kStatusTimeout = 4;                 // value of HSG_ETIMEOUT
 constexpr long long kCleanupWait = 2000000000LL;  // cycles, per outstanding copy
@@ -143,43 +143,32 @@ __device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) 
     for (int v = 0; v < V; ++v) d[c][v] = s[c][v];
 }
 
-// Local field of the site of x-parity `a` in pair k of row y, plane pl:
-// h = sum over its six bonds of J s_neighbour (J symmetric).  `partner` is
-// the other site of the pair, `ext` the x-neighbour outside the pair, `yu`,
-// `yd`, `zu`, `zd` the neighbours at y+1, y-1, z+1, z-1.
+// Local field h = sum over the six bonds of J s_neighbour (J symmetric) of
+// one site, in the order +x, -x, +y, -y, +z, -z.  Jb points at the sample's
+// couplings; pos, pos_xm, pos_ym, pos_zm are the storage positions of the
+// site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds are
+// this site's -x, -y, -z bonds).
 template <int V, int PREC>
-__device__ __forceinline__ void pair_field(const void* J, size_t jb, int N, int L, int half, int pl, int pl_dn,
-                                           int y, int y_dn, int a, int k, int k_dn, const float (&partner)[3][V],
-                                           const float (&ext)[3][V], const float (&yu)[3][V],
-                                           const float (&yd)[3][V], const float (&zu)[3][V],
-                                           const float (&zd)[3][V], float (&h)[3][V]) {
+__device__ __forceinline__ void site_field(const void* Jb, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
+                                           const float (&xp)[3][V], const float (&xm)[3][V],
+                                           const float (&yu)[3][V], const float (&yd)[3][V],
+                                           const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int v = 0; v < V; ++v) h[c][v] = 0.0f;
-  const int row = (pl * L + y) * L;
-  const int pos = row + a * half + k;                            // this site
-  const int pos_xm = (a == 1) ? row + k : row + half + k_dn;     // site at x-1
-  float xp[3][V], xm[3][V];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      xp[c][v] = (a == 0) ? partner[c][v] : ext[c][v];   // neighbour at x+1
-      xm[c][v] = (a == 0) ? ext[c][v] : partner[c][v];   // neighbour at x-1
-    }
   float j[6];
-  load_bond<PREC>(J, jb + pos, j);
+  load_bond<PREC>(Jb, pos, j);
   add_bond<V>(j, xp, h);
-  load_bond<PREC>(J, jb + pos_xm, j);
+  load_bond<PREC>(Jb, pos_xm, j);
   add_bond<V>(j, xm, h);
-  load_bond<PREC>(J, jb + N + pos, j);
+  load_bond<PREC>(Jb, N + pos, j);
   add_bond<V>(j, yu, h);
-  load_bond<PREC>(J, jb + N + (pl * L + y_dn) * L + a * half + k, j);
+  load_bond<PREC>(Jb, N + pos_ym, j);
   add_bond<V>(j, yd, h);
-  load_bond<PREC>(J, jb + 2 * static_cast<size_t>(N) + pos, j);
+  load_bond<PREC>(Jb, 2 * N + pos, j);
   add_bond<V>(j, zu, h);
-  load_bond<PREC>(J, jb + 2 * static_cast<size_t>(N) + (pl_dn * L + y) * L + a * half + k, j);
+  load_bond<PREC>(Jb, 2 * N + pos_zm, j);
   add_bond<V>(j, zd, h);
 }
 
@@ -202,10 +191,11 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
 }
 
 template <int KIND, int V, int PREC>
-__global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams p) {
+__global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[kFusedSlots + 1];  // [kFusedSlots]: never completed
   __shared__ double s_red[V][kFusedMaxThreads / 32];
+  __shared__ int s_failed;
 
   const int L = p.L, half = L >> 1, N = p.N;
   const bool full = (p.band_rows == L);
@@ -234,7 +224,13 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams
   const float* in_g = p.in + gbase;
   float* out_g = p.out + gbase;
   const size_t plane_g = static_cast<size_t>(N) * V;   // component stride in global memory
-  const size_t jb = static_cast<size_t>(sb) * 3 * N;
+  // couplings of this sample (element size depends on the storage precision)
+  const void* Jb = (PREC == kPrecF16)
+                       ? static_cast<const void*>(static_cast<const uint4*>(p.J) + static_cast<size_t>(sb) * 3 * N)
+                       : static_cast<const void*>(static_cast<const float*>(p.J) + static_cast<size_t>(sb) * 3 * N * 6);
+  const bool want_energy = (p.e_partial != nullptr);
+  const int LL = L * L;
+  const int yrow = y * L, ydrow = y_dn * L;
 
   float beta[V];
   uint32_t lat0 = 0, t_hb = 0;
@@ -277,6 +273,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams
   if (tid == 0) {
     for (int s = 0; s <= kFusedSlots; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_failed = 0;
   }
   __syncthreads();
   int issued = -2;  // highest virtual plane issued (meaningful in thread 0)
@@ -310,12 +307,9 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams
   }
 
   for (int z = 0; !failed && z <= L + 1; ++z) {
-    ok = mbar_wait_bounded(&bars[(z + 2) & 3], parity_of(z + 1), p.timeout);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    first_unwaited = z + 2;
+    // A thread whose wait expires flags the CTA; everyone sees the flag after
+    // this step's barrier (the step's results are then discarded).
+    if (!mbar_wait_bounded(&bars[(z + 2) & 3], parity_of(z + 1), p.timeout)) s_failed = 1;
     const int pz = z % L;
     if (active) {
       const int ab1 = (y + pz + 1) & 1;
@@ -325,11 +319,18 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams
       // black site of plane z (x-parity ab) from the old white spins
       const int ab = (y + pz) & 1;
       const int pz_dn = (pz == 0) ? L - 1 : pz - 1;
-      float ext[3][V], yu[3][V], yd[3][V], h[3][V];
-      lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k_dn), ext, comp_f);
+      float xp[3][V], xm[3][V], yu[3][V], yd[3][V], h[3][V];
+      lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f);
+      lds_site<V>(at(z, r, ab ^ 1, ab ? k : k_dn), xm, comp_f);
       lds_site<V>(at(z, r_up, ab, k), yu, comp_f);
       lds_site<V>(at(z, r_dn, ab, k), yd, comp_f);
-      pair_field<V, PREC>(p.J, jb, N, L, half, pz, pz_dn, y, y_dn, ab, k, k_dn, W0, ext, yu, yd, Wp1, Wm1, h);
+      {
+        const int pl = pz * LL;
+        const int pos = pl + yrow + ab * half + k;
+        const int pos_xm = pl + yrow + (ab ? k : half + k_dn);
+        site_field<V, PREC>(Jb, N, pos, pos_xm, pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k,
+                            xp, xm, yu, yd, Wp1, Wm1, h);
+      }
       const uint32_t i_nat = static_cast<uint32_t>(2 * k + ab + L * (y + L * pz));
       update_site<KIND, V>(h, B0, beta, i_nat, lat0, t_hb, p.key);
       sts_site<V>(at(z, r, ab, k), B0, comp_f);
@@ -339,24 +340,36 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 1) k_sweep_fused(FusedParams
         const int q = (z - 1) % L;
         const int q_dn = (q == 0) ? L - 1 : q - 1;
         const int aw = ((y + q) & 1) ^ 1;
-        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k_up : k_dn), ext, comp_f);
+        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k_up : k), xp, comp_f);
+        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k : k_dn), xm, comp_f);
         lds_site<V>(at(z - 1, r_up, aw, k), yu, comp_f);
         lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
-        pair_field<V, PREC>(p.J, jb, N, L, half, q, q_dn, y, y_dn, aw, k, k_dn, Bm1, ext, yu, yd, B0, Bm2, h);
+        const int pl = q * LL;
+        const int pos = pl + yrow + aw * half + k;
+        const int pos_xm = pl + yrow + (aw ? k : half + k_dn);
+        site_field<V, PREC>(Jb, N, pos, pos_xm, pl + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k,
+                            xp, xm, yu, yd, B0, Bm2, h);
         const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));
         update_site<KIND, V>(h, Wm1, beta, iw_nat, lat0, t_hb, p.key);
+        if (want_energy) {
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          e_acc[v] += static_cast<double>(fmaf(Wm1[0][v], h[0][v], fmaf(Wm1[1][v], h[1][v], Wm1[2][v] * h[2][v])));
-        float* dst = out_g + (static_cast<size_t>(q * L + y) * L) * V;
-        stg_site<V>(dst + (static_cast<size_t>((aw ^ 1) * half + k)) * V, Bm1, plane_g);
-        stg_site<V>(dst + (static_cast<size_t>(aw * half + k)) * V, Wm1, plane_g);
+          for (int v = 0; v < V; ++v)
+            e_acc[v] += static_cast<double>(fmaf(Wm1[0][v], h[0][v], fmaf(Wm1[1][v], h[1][v], Wm1[2][v] * h[2][v])));
+        }
+        float* dst = out_g + static_cast<size_t>(pl + yrow) * V;
+        stg_site<V>(dst + ((aw ^ 1) * half + k) * V, Bm1, plane_g);
+        stg_site<V>(dst + (aw * half + k) * V, Wm1, plane_g);
       }
     }
     // Generic-proxy accesses of the slot being refilled must precede the
     // asynchronous copy that overwrites it.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (s_failed) {
+      failed = true;
+      break;
+    }
+    first_unwaited = z + 2;
     if (tid == 0 && z + 3 <= L + 2) {
       issue(z + 3);
       issued = z + 3;

@@ -91,14 +91,33 @@ __device__ __forceinline__ void store_spin(float* base, size_t plane, int i, con
   }
 }
 
-// h += J s for the symmetric J = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]].
+// h += J s for the symmetric J = [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]].  With
+// two interleaved lattices the pair (lattice 0, lattice 1) is one packed
+// FP32x2 fused multiply-add per matrix element (same rounding per lane as
+// fmaf, so results do not depend on V).
 template <int V>
 __device__ __forceinline__ void add_bond(const float (&j)[6], const float (&s)[3][V], float (&h)[3][V]) {
+  if constexpr (V == 2) {
+    const float2 s0 = make_float2(s[0][0], s[0][1]), s1 = make_float2(s[1][0], s[1][1]),
+                 s2 = make_float2(s[2][0], s[2][1]);
+    float2 h0 = make_float2(h[0][0], h[0][1]), h1 = make_float2(h[1][0], h[1][1]),
+           h2 = make_float2(h[2][0], h[2][1]);
+    h0 = __ffma2_rn(make_float2(j[0], j[0]), s0,
+                    __ffma2_rn(make_float2(j[3], j[3]), s1, __ffma2_rn(make_float2(j[4], j[4]), s2, h0)));
+    h1 = __ffma2_rn(make_float2(j[3], j[3]), s0,
+                    __ffma2_rn(make_float2(j[1], j[1]), s1, __ffma2_rn(make_float2(j[5], j[5]), s2, h1)));
+    h2 = __ffma2_rn(make_float2(j[4], j[4]), s0,
+                    __ffma2_rn(make_float2(j[5], j[5]), s1, __ffma2_rn(make_float2(j[2], j[2]), s2, h2)));
+    h[0][0] = h0.x; h[0][1] = h0.y;
+    h[1][0] = h1.x; h[1][1] = h1.y;
+    h[2][0] = h2.x; h[2][1] = h2.y;
+  } else {
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    h[0][v] = fmaf(j[0], s[0][v], fmaf(j[3], s[1][v], fmaf(j[4], s[2][v], h[0][v])));
-    h[1][v] = fmaf(j[3], s[0][v], fmaf(j[1], s[1][v], fmaf(j[5], s[2][v], h[1][v])));
-    h[2][v] = fmaf(j[4], s[0][v], fmaf(j[5], s[1][v], fmaf(j[2], s[2][v], h[2][v])));
+    for (int v = 0; v < V; ++v) {
+      h[0][v] = fmaf(j[0], s[0][v], fmaf(j[3], s[1][v], fmaf(j[4], s[2][v], h[0][v])));
+      h[1][v] = fmaf(j[3], s[0][v], fmaf(j[1], s[1][v], fmaf(j[5], s[2][v], h[1][v])));
+      h[2][v] = fmaf(j[4], s[0][v], fmaf(j[5], s[1][v], fmaf(j[2], s[2][v], h[2][v])));
+    }
   }
 }
 
@@ -159,7 +178,7 @@ __device__ __forceinline__ void overrelax(float hx, float hy, float hz, float& s
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
   if (hh > 0.0f) {
     const float hs = fmaf(hx, sx, fmaf(hy, sy, hz * sz));
-    const float f = 2.0f * hs / hh;
+    const float f = __fdividef(2.0f * hs, hh);  // |h|^2 is O(1..100): well inside its range
     sx = fmaf(f, hx, -sx);
     sy = fmaf(f, hy, -sy);
     sz = fmaf(f, hz, -sz);
