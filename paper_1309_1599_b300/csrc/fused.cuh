@@ -144,32 +144,43 @@ __device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) 
 }
 
 // Local field h = sum over the six bonds of J s_neighbour (J symmetric) of
-// one site, in the order +x, -x, +y, -y, +z, -z.  Jb points at the sample's
-// couplings; pos, pos_xm, pos_ym, pos_zm are the storage positions of the
-// site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds are
-// this site's -x, -y, -z bonds).
+// one site, accumulated as in k_sweep_half (forward bonds x+1, y+1, z+1 and
+// backward bonds x-1, y-1, z-1 in two partial sums).  Jb points at the
+// sample's couplings; pos, pos_xm, pos_ym, pos_zm are the storage positions
+// of the site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds
+// are this site's -x, -y, -z bonds).
 template <int V, int PREC>
 __device__ __forceinline__ void site_field(const void* Jb, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
                                            const float (&xp)[3][V], const float (&xm)[3][V],
                                            const float (&yu)[3][V], const float (&yd)[3][V],
                                            const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int v = 0; v < V; ++v) h[c][v] = 0.0f;
-  float j[6];
+  float hf[3][V], hb[3][V], j[6];
+  zero3<V>(hf);
+  zero3<V>(hb);
   load_bond<PREC>(Jb, pos, j);
-  add_bond<V>(j, xp, h);
-  load_bond<PREC>(Jb, pos_xm, j);
-  add_bond<V>(j, xm, h);
+  add_bond<V>(j, xp, hf);
   load_bond<PREC>(Jb, N + pos, j);
-  add_bond<V>(j, yu, h);
-  load_bond<PREC>(Jb, N + pos_ym, j);
-  add_bond<V>(j, yd, h);
+  add_bond<V>(j, yu, hf);
   load_bond<PREC>(Jb, 2 * N + pos, j);
-  add_bond<V>(j, zu, h);
+  add_bond<V>(j, zu, hf);
+  load_bond<PREC>(Jb, pos_xm, j);
+  add_bond<V>(j, xm, hb);
+  load_bond<PREC>(Jb, N + pos_ym, j);
+  add_bond<V>(j, yd, hb);
   load_bond<PREC>(Jb, 2 * N + pos_zm, j);
-  add_bond<V>(j, zd, h);
+  add_bond<V>(j, zd, hb);
+  combine_field<V>(hf, hb, h);
+}
+
+// Pulls the six bonds of a site into L1 ahead of site_field.
+template <int PREC>
+__device__ __forceinline__ void prefetch_bonds(const void* Jb, int N, int pos, int pos_xm, int pos_ym, int pos_zm) {
+  const int idx[6] = {pos, N + pos, 2 * N + pos, pos_xm, N + pos_ym, 2 * N + pos_zm};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if constexpr (PREC == kPrecF16) prefetch_l1(static_cast<const uint4*>(Jb) + idx[q]);
+    else prefetch_l1(static_cast<const float*>(Jb) + static_cast<size_t>(idx[q]) * 6);
+  }
 }
 
 template <int KIND, int V>
@@ -191,7 +202,7 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
 }
 
 template <int KIND, int V, int PREC>
-__global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
+__global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[kFusedSlots + 1];  // [kFusedSlots]: never completed
   __shared__ double s_red[V][kFusedMaxThreads / 32];
@@ -282,9 +293,14 @@ __global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
     issued = 2;
   }
 
-  // Register window of this thread's pair: black / white sites at planes
-  // z-2 (black only), z-1, z, z+1.
-  float Bm2[3][V], Bm1[3][V], Wm1[3][V], B0[3][V], W0[3][V], Bp1[3][V], Wp1[3][V];
+  // Registers hold only the new black spins of this thread's column at the
+  // two previous planes (their slots are refilled before they are needed
+  // again) and of the current plane; everything else is read from the
+  // resident slots: planes z-1, z (in-plane neighbours, old white spins,
+  // new black spins) and z+1.
+  float Bm2[3][V], Bm1[3][V], B0[3][V];
+  zero3<V>(Bm2);
+  zero3<V>(Bm1);
   double e_acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) e_acc[v] = 0.0;
@@ -296,15 +312,6 @@ __global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
   ok = ok && mbar_wait_bounded(&bars[1], parity_of(0), p.timeout);
   bool failed = __syncthreads_or(!ok) != 0;
   if (!failed) first_unwaited = 1;
-  if (!failed && active) {
-    const int ab_m1 = (y + L - 1) & 1;  // black x-parity at plane L-1
-    lds_site<V>(at(-1, r, ab_m1, k), Bm1, comp_f);
-    lds_site<V>(at(-1, r, ab_m1 ^ 1, k), Wm1, comp_f);
-    const int ab_0 = y & 1;
-    lds_site<V>(at(0, r, ab_0, k), B0, comp_f);
-    lds_site<V>(at(0, r, ab_0 ^ 1, k), W0, comp_f);
-    copy3<V>(Bm2, Bm1);
-  }
 
   for (int z = 0; !failed && z <= L + 1; ++z) {
     // A thread whose wait expires flags the CTA; everyone sees the flag after
@@ -312,53 +319,57 @@ __global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
     if (!mbar_wait_bounded(&bars[(z + 2) & 3], parity_of(z + 1), p.timeout)) s_failed = 1;
     const int pz = z % L;
     if (active) {
-      const int ab1 = (y + pz + 1) & 1;
-      lds_site<V>(at(z + 1, r, ab1, k), Bp1, comp_f);
-      lds_site<V>(at(z + 1, r, ab1 ^ 1, k), Wp1, comp_f);
-
-      // black site of plane z (x-parity ab) from the old white spins
+      // black site of plane z: x-parity ab, from the old white spins; its
+      // column's white sites at z-1 and z+1 have the same x-parity
       const int ab = (y + pz) & 1;
       const int pz_dn = (pz == 0) ? L - 1 : pz - 1;
-      float xp[3][V], xm[3][V], yu[3][V], yd[3][V], h[3][V];
+      const bool do_white = (z >= 2 && owner);
+      const int q = (z + L - 1) % L;  // plane of the white update
+      const int q_dn = (q == 0) ? L - 1 : q - 1;
+      const int aw = ab;              // white site of plane z-1 in this column
+      const int plq = q * LL;
+      if (do_white)
+        prefetch_bonds<PREC>(Jb, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
+                             plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k);
+      float xp[3][V], xm[3][V], yu[3][V], yd[3][V], zu[3][V], zd[3][V], h[3][V];
+      lds_site<V>(at(z, r, ab, k), B0, comp_f);
       lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f);
       lds_site<V>(at(z, r, ab ^ 1, ab ? k : k_dn), xm, comp_f);
       lds_site<V>(at(z, r_up, ab, k), yu, comp_f);
       lds_site<V>(at(z, r_dn, ab, k), yd, comp_f);
+      lds_site<V>(at(z + 1, r, ab, k), zu, comp_f);
+      lds_site<V>(at(z - 1, r, ab, k), zd, comp_f);
       {
         const int pl = pz * LL;
-        const int pos = pl + yrow + ab * half + k;
-        const int pos_xm = pl + yrow + (ab ? k : half + k_dn);
-        site_field<V, PREC>(Jb, N, pos, pos_xm, pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k,
-                            xp, xm, yu, yd, Wp1, Wm1, h);
+        site_field<V, PREC>(Jb, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
+                            pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k, xp, xm, yu, yd, zu,
+                            zd, h);
       }
       const uint32_t i_nat = static_cast<uint32_t>(2 * k + ab + L * (y + L * pz));
       update_site<KIND, V>(h, B0, beta, i_nat, lat0, t_hb, p.key);
       sts_site<V>(at(z, r, ab, k), B0, comp_f);
 
       // white site of plane z-1 from the new black spins
-      if (z >= 2 && owner) {
-        const int q = (z - 1) % L;
-        const int q_dn = (q == 0) ? L - 1 : q - 1;
-        const int aw = ((y + q) & 1) ^ 1;
+      if (do_white) {
+        float w[3][V];
+        lds_site<V>(at(z - 1, r, aw, k), w, comp_f);
         lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k_up : k), xp, comp_f);
         lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k : k_dn), xm, comp_f);
         lds_site<V>(at(z - 1, r_up, aw, k), yu, comp_f);
         lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
-        const int pl = q * LL;
-        const int pos = pl + yrow + aw * half + k;
-        const int pos_xm = pl + yrow + (aw ? k : half + k_dn);
-        site_field<V, PREC>(Jb, N, pos, pos_xm, pl + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k,
-                            xp, xm, yu, yd, B0, Bm2, h);
+        site_field<V, PREC>(Jb, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
+                            plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k, xp, xm, yu, yd, B0,
+                            Bm2, h);
         const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));
-        update_site<KIND, V>(h, Wm1, beta, iw_nat, lat0, t_hb, p.key);
+        update_site<KIND, V>(h, w, beta, iw_nat, lat0, t_hb, p.key);
         if (want_energy) {
 #pragma unroll
           for (int v = 0; v < V; ++v)
-            e_acc[v] += static_cast<double>(fmaf(Wm1[0][v], h[0][v], fmaf(Wm1[1][v], h[1][v], Wm1[2][v] * h[2][v])));
+            e_acc[v] += static_cast<double>(fmaf(w[0][v], h[0][v], fmaf(w[1][v], h[1][v], w[2][v] * h[2][v])));
         }
-        float* dst = out_g + static_cast<size_t>(pl + yrow) * V;
+        float* dst = out_g + static_cast<size_t>(plq + yrow) * V;
         stg_site<V>(dst + ((aw ^ 1) * half + k) * V, Bm1, plane_g);
-        stg_site<V>(dst + (aw * half + k) * V, Wm1, plane_g);
+        stg_site<V>(dst + (aw * half + k) * V, w, plane_g);
       }
     }
     // Generic-proxy accesses of the slot being refilled must precede the
@@ -376,9 +387,6 @@ __global__ void __maxnreg__(112) k_sweep_fused(FusedParams p) {
     }
     copy3<V>(Bm2, Bm1);
     copy3<V>(Bm1, B0);
-    copy3<V>(Wm1, W0);
-    copy3<V>(B0, Bp1);
-    copy3<V>(W0, Wp1);
   }
 
   if (failed) {

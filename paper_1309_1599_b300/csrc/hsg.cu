@@ -251,6 +251,36 @@ hsg_status allow_fused_smem(size_t bytes) {
   return HSG_OK;
 }
 
+template <int KIND, int V, int PREC>
+int fused_max_threads_one() {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, k_sweep_fused<KIND, V, PREC>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return a.maxThreadsPerBlock;
+}
+
+// Largest block the fused kernels (heat-bath and overrelaxation) can launch
+// with, as the driver reports it for their register use; 0 if unknown.
+int fused_max_threads(int V, int prec) {
+  int a, b;
+  if (V == 2 && prec == HSG_F16) {
+    a = fused_max_threads_one<kHB, 2, kPrecF16>();
+    b = fused_max_threads_one<kOR, 2, kPrecF16>();
+  } else if (V == 2) {
+    a = fused_max_threads_one<kHB, 2, kPrecF32>();
+    b = fused_max_threads_one<kOR, 2, kPrecF32>();
+  } else if (prec == HSG_F16) {
+    a = fused_max_threads_one<kHB, 1, kPrecF16>();
+    b = fused_max_threads_one<kOR, 1, kPrecF16>();
+  } else {
+    a = fused_max_threads_one<kHB, 1, kPrecF32>();
+    b = fused_max_threads_one<kOR, 1, kPrecF32>();
+  }
+  return std::min(std::min(a, b), kFusedMaxThreads);
+}
+
 hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
   if (V == 2 && prec == HSG_F16) {
     HSG_TRY((allow_fused_smem<kHB, 2, kPrecF16>(bytes)));
@@ -272,11 +302,13 @@ hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
 // whole planes if they fit, else the widest band of rows (a divisor of L, at
 // least 8) within the thread and shared-memory limits.  False: use the
 // two-pass half-sweep kernel.
-bool plan_fused(int L, int V, int* band_rows, size_t* smem) {
+bool plan_fused(int L, int V, int max_threads, int* band_rows, size_t* smem) {
   const size_t max_smem = 200 * 1024;
   auto smem_for = [&](int rows) { return static_cast<size_t>(kFusedSlots) * 3 * rows * L * V * sizeof(float); };
-  auto threads_for = [&](int rows) { return rows * (L / 2); };
-  if (threads_for(L) <= kFusedMaxThreads && smem_for(L) <= max_smem) {
+  // blocks are rounded up to whole warps
+  auto threads_for = [&](int rows) { return (rows * (L / 2) + 31) / 32 * 32; };
+  if (max_threads <= 0) return false;
+  if (threads_for(L) <= max_threads && smem_for(L) <= max_smem) {
     *band_rows = L;
     *smem = smem_for(L);
     return true;
@@ -284,7 +316,7 @@ bool plan_fused(int L, int V, int* band_rows, size_t* smem) {
   if ((L * V) % 4 != 0) return false;  // 16-byte rows for the bulk copies
   for (int B = L / 2; B >= 8; --B) {
     if (L % B != 0) continue;
-    if (threads_for(B + 2) <= kFusedMaxThreads && smem_for(B + 4) <= max_smem) {
+    if (threads_for(B + 2) <= max_threads && smem_for(B + 4) <= max_smem) {
       *band_rows = B;
       *smem = smem_for(B + 4);
       return true;
@@ -550,7 +582,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     b.S_b = static_cast<int>(b.samples.size());
     b.G = h->R / V;
     b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
-    b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) && plan_fused(b.L, V, &b.band_rows, &b.fused_smem);
+    b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) &&
+              plan_fused(b.L, V, fused_max_threads(V, h->prec), &b.band_rows, &b.fused_smem);
     b.n_bands = b.fused ? b.L / b.band_rows : 0;
     // the shared-memory limit is a property of the kernel, not of the bucket:
     // raise it to what the largest tiling in this context needs
