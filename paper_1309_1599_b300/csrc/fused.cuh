@@ -196,8 +196,7 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
       heat_bath_draw(h[0][v], h[1][v], h[2][v], beta[v], w0, w1, s[0][v], s[1][v], s[2][v]);
     }
   } else {
-#pragma unroll
-    for (int v = 0; v < V; ++v) overrelax(h[0][v], h[1][v], h[2][v], s[0][v], s[1][v], s[2][v]);
+    overrelax_v<V>(h, s);
   }
 }
 
@@ -328,9 +327,18 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       const int q_dn = (q == 0) ? L - 1 : q - 1;
       const int aw = ab;              // white site of plane z-1 in this column
       const int plq = q * LL;
-      if (do_white)
-        prefetch_bonds<PREC>(Jb, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
-                             plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k);
+      {
+        // bonds of the next step's sites into L1: black site of plane z+1
+        // and white site of plane z (both of x-parity ab ^ 1)
+        const int an = ab ^ 1;
+        const int pn = (pz + 1 == L) ? 0 : pz + 1;
+        const int pln = pn * LL, plz = pz * LL;
+        prefetch_bonds<PREC>(Jb, N, pln + yrow + an * half + k, pln + yrow + (an ? k : half + k_dn),
+                             pln + ydrow + an * half + k, plz + yrow + an * half + k);
+        if (owner && z >= 1)
+          prefetch_bonds<PREC>(Jb, N, plz + yrow + an * half + k, plz + yrow + (an ? k : half + k_dn),
+                               plz + ydrow + an * half + k, pz_dn * LL + yrow + an * half + k);
+      }
       float xp[3][V], xm[3][V], yu[3][V], yd[3][V], zu[3][V], zd[3][V], h[3][V];
       lds_site<V>(at(z, r, ab, k), B0, comp_f);
       lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f);

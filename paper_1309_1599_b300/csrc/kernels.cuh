@@ -185,6 +185,33 @@ __device__ __forceinline__ void overrelax(float hx, float hy, float hz, float& s
   }
 }
 
+// Overrelaxation of V lattices at once (the two interleaved lattices share
+// packed FP32x2 arithmetic; each lane rounds exactly like overrelax()).
+template <int V>
+__device__ __forceinline__ void overrelax_v(const float (&h)[3][V], float (&s)[3][V]) {
+  if constexpr (V == 2) {
+    const float2 hx = make_float2(h[0][0], h[0][1]), hy = make_float2(h[1][0], h[1][1]),
+                 hz = make_float2(h[2][0], h[2][1]);
+    const float2 sx = make_float2(s[0][0], s[0][1]), sy = make_float2(s[1][0], s[1][1]),
+                 sz = make_float2(s[2][0], s[2][1]);
+    const float2 hh = __ffma2_rn(hx, hx, __ffma2_rn(hy, hy, __fmul2_rn(hz, hz)));
+    const float2 hs = __ffma2_rn(hx, sx, __ffma2_rn(hy, sy, __fmul2_rn(hz, sz)));
+    const float2 f = make_float2(__fdividef(2.0f * hs.x, hh.x), __fdividef(2.0f * hs.y, hh.y));
+    const float2 nx = __ffma2_rn(f, hx, make_float2(-sx.x, -sx.y));
+    const float2 ny = __ffma2_rn(f, hy, make_float2(-sy.x, -sy.y));
+    const float2 nz = __ffma2_rn(f, hz, make_float2(-sz.x, -sz.y));
+    if (hh.x > 0.0f) {
+      s[0][0] = nx.x; s[1][0] = ny.x; s[2][0] = nz.x;
+    }
+    if (hh.y > 0.0f) {
+      s[0][1] = nx.y; s[1][1] = ny.y; s[2][1] = nz.y;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) overrelax(h[0][v], h[1][v], h[2][v], s[0][v], s[1][v], s[2][v]);
+  }
+}
+
 // Storage index of site (x, row) with row = y + L*z: parity-split when SPLIT,
 // natural order x + L*row otherwise.
 template <bool SPLIT>
@@ -296,8 +323,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
       float o[3][V];
       load_spin<V>(base, plane, i, o);
       if constexpr (KIND == kOR) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) overrelax(h[0][v], h[1][v], h[2][v], o[0][v], o[1][v], o[2][v]);
+        overrelax_v<V>(h, o);
         store_spin<V>(base, plane, i, o);
       }
 #pragma unroll
