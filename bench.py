@@ -185,9 +185,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # the hsg arm
 # ----------------------------------------------------------------------------
-def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1):
+def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0):
     lat = hsg.Lattice([w["L"]] * len(samples), beta, n_replicas=w["n_rep"], coupling_prec=prec,
-                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed)
+                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed,
+                      band_rows=band_rows)
     for s in range(len(samples)):
         lat.set_couplings(s, J[s])
         for j in range(lat.R):
@@ -235,9 +236,9 @@ def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
     return e0.elapsed_time(e1) / (n_calls * per_sweep * sweeps)
 
 
-def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak):
+def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0):
     samples, J, spins, beta = inputs
-    lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout)
+    lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows)
     N, R, S = w["L"] ** 3, lat.R, len(samples)
     for _ in range(warmup):
         lat.run_steps(MCS_PER_STEP)
@@ -378,6 +379,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
+    ap.add_argument("--band-rows", type=int, default=0,
+                    help="rows per CTA band of the fused sweep (0: library choice)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world, rank, local = dist_env()
@@ -393,7 +396,7 @@ def main():
 
     sampler = ClockSampler(local)
     batched = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
-                       args.warmup, sampler, peak)
+                       args.warmup, sampler, peak, band_rows=args.band_rows)
     batched["lat"].destroy()
     plain = None
     if not args.no_plain:

@@ -108,6 +108,9 @@ typedef struct {
   long long timeout_cycles; /* bound (SM clock cycles) for each device-side wait,
                               0 = library default (4e9) */
   int sweep_kernel;       /* HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS */
+  int band_rows;          /* fused sweep: rows per CTA band, 0 = library choice;
+                             otherwise L or a divisor of L >= 8 that fits the
+                             block and shared-memory limits (HSG_EINVAL if not) */
 } hsg_config;
 
 /* Create a context: validates cfg (copied; the caller's arrays may be freed

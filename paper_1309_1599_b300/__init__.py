@@ -49,7 +49,8 @@ class _Config(ctypes.Structure):
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("coupling_prec", ctypes.c_int),
                 ("layout", ctypes.c_int), ("n_or", ctypes.c_int), ("measure_every", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int)]
+                ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int),
+                ("band_rows", ctypes.c_int)]
 
 
 _SIGNATURES = {
@@ -144,7 +145,7 @@ class Lattice:
 
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
-                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO):
+                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0):
         lib = load_library()
         _require_gpu()
         if np.isscalar(L):
@@ -172,6 +173,7 @@ class Lattice:
         cfg.stream = _current_stream() if stream is None else ctypes.c_void_p(stream)
         cfg.timeout_cycles = int(timeout_cycles)
         cfg.sweep_kernel = int(sweep_kernel)
+        cfg.band_rows = int(band_rows)
         h = ctypes.c_void_p()
         _check(lib.hsg_lattice_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -302,12 +302,21 @@ hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
 // whole planes if they fit, else the widest band of rows (a divisor of L, at
 // least 8) within the thread and shared-memory limits.  False: use the
 // two-pass half-sweep kernel.
-bool plan_fused(int L, int V, int max_threads, int* band_rows, size_t* smem) {
+bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t* smem) {
   const size_t max_smem = 200 * 1024;
   auto smem_for = [&](int rows) { return static_cast<size_t>(kFusedSlots) * 3 * rows * L * V * sizeof(float); };
   // blocks are rounded up to whole warps
   auto threads_for = [&](int rows) { return (rows * (L / 2) + 31) / 32 * 32; };
   if (max_threads <= 0) return false;
+  if (want > 0) {  // a requested band: whole planes, or a divisor of L of at least 8 rows
+    const bool full = (want == L);
+    if (!full && (want < 8 || L % want != 0 || (L * V) % 4 != 0)) return false;
+    const int rows_t = full ? L : want + 2, rows_s = full ? L : want + 4;
+    if (threads_for(rows_t) > max_threads || smem_for(rows_s) > max_smem) return false;
+    *band_rows = want;
+    *smem = smem_for(rows_s);
+    return true;
+  }
   if (threads_for(L) <= max_threads && smem_for(L) <= max_smem) {
     *band_rows = L;
     *smem = smem_for(L);
@@ -513,6 +522,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   if (cfg->n_or < 0 || cfg->measure_every < 0) return fail(HSG_EINVAL, "n_or and measure_every must be >= 0");
   if (cfg->sweep_kernel != HSG_SWEEP_AUTO && cfg->sweep_kernel != HSG_SWEEP_TWO_PASS)
     return fail(HSG_EINVAL, "sweep_kernel must be HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS");
+  if (cfg->band_rows < 0 || (cfg->band_rows > 0 && cfg->sweep_kernel != HSG_SWEEP_AUTO))
+    return fail(HSG_EINVAL, "band_rows must be 0, or > 0 with the fused sweep");
   for (int s = 0; s < cfg->n_samples; ++s) {
     const int L = cfg->L[s];
     if (L < 4 || L > 512 || (L & 1)) return fail(HSG_EINVAL, "each L must be even and in [4, 512]");
@@ -583,7 +594,11 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     b.G = h->R / V;
     b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
     b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) &&
-              plan_fused(b.L, V, fused_max_threads(V, h->prec), &b.band_rows, &b.fused_smem);
+              plan_fused(b.L, V, fused_max_threads(V, h->prec), cfg->band_rows, &b.band_rows, &b.fused_smem);
+    if (cfg->band_rows > 0 && !b.fused) {
+      fail(HSG_EINVAL, "band_rows does not tile L = " + std::to_string(b.L) + " within the limits");
+      return bail(HSG_EINVAL);
+    }
     b.n_bands = b.fused ? b.L / b.band_rows : 0;
     // the shared-memory limit is a property of the kernel, not of the bucket:
     // raise it to what the largest tiling in this context needs

@@ -132,7 +132,8 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
                                                uint32_t w0, uint32_t w1,
                                                float& sx, float& sy, float& sz) {
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-  const float hn = sqrtf(hh);
+  const float inv = (hh > 0.0f) ? rsqrtf(hh) : 0.0f;   // 1/|h| (2 ulp)
+  const float hn = hh * inv;
   const float kappa = beta * hn;
   const float r0 = uniform23(w0);
   const float r1 = uniform23(w1);
@@ -141,29 +142,42 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
   // close to 1 (expm1 rounds to -1 and 1 - y cancels), so the two regimes are
   // evaluated separately: log1p(-y) for y < 1/2, and for y >= 1/2 the
   // logarithm of 1 - y = (1 - r0) + r0 e^{-2 kappa}, a sum of two positive
-  // terms in which 1 - r0 is exact.
+  // terms in which 1 - r0 is exact.  For kappa > 1/2, 1 - e^{-2 kappa} >= 0.63
+  // cannot cancel, so the fast exponential serves both terms; expm1 is kept
+  // for small kappa, where 1 - e^{-2 kappa} is small.
   float w;
   if (kappa < 1e-30f) {
     w = 2.0f * r0;
   } else {
-    const float y = -r0 * expm1f(-2.0f * kappa);
-    const float lg = (y < 0.5f) ? log1pf(-y) : logf(fmaf(r0, expf(-2.0f * kappa), 1.0f - r0));
-    w = -lg / kappa;
+    float y, e2k;
+    if (kappa > 0.5f) {
+      e2k = __expf(-2.0f * kappa);
+      y = fmaf(-r0, e2k, r0);
+    } else {
+      const float em = expm1f(-2.0f * kappa);
+      e2k = em + 1.0f;
+      y = -r0 * em;
+    }
+    const float lg = (y < 0.5f) ? log1pf(-y) : logf(fmaf(r0, e2k, 1.0f - r0));
+    w = __fdividef(-lg, kappa);
   }
   w = fminf(fmaxf(w, 0.0f), 2.0f);
   const float u = 1.0f - w;
   const float st = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
+  // azimuth phi = 2 pi r1: evaluated as phi - pi in (-pi, pi), where the
+  // fast sine and cosine are accurate to 2^-21.4, then reflected
   float sp, cp;
-  sincospif(2.0f * r1, &sp, &cp);
+  __sincosf(6.283185307179586f * (r1 - 0.5f), &sp, &cp);
+  sp = -sp;
+  cp = -cp;
   float nx = 0.0f, ny = 0.0f, nz = 1.0f;
-  if (hn > 0.0f) {
-    const float inv = 1.0f / hn;
+  if (hh > 0.0f) {
     nx = hx * inv;
     ny = hy * inv;
     nz = hz * inv;
   }
   const float sgn = copysignf(1.0f, nz);
-  const float p = -1.0f / (sgn + nz);
+  const float p = __fdividef(-1.0f, sgn + nz);   // |sgn + nz| in [1, 2]
   const float q = nx * ny * p;
   const float e1x = fmaf(sgn * nx * nx, p, 1.0f), e1y = sgn * q, e1z = -sgn * nx;
   const float e2x = q, e2y = fmaf(ny * ny, p, sgn), e2z = -ny;

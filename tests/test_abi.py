@@ -51,6 +51,7 @@ def _cfg(**kw):
     c.stream = None
     c.timeout_cycles = 0
     c.sweep_kernel = kw.pop("sweep_kernel", 0)
+    c.band_rows = kw.pop("band_rows", 0)
     return c, (L, beta)
 
 
@@ -61,6 +62,8 @@ def _cfg(**kw):
     (dict(layout=1, n_replicas=1, beta=[1.0]), "even number"),
     (dict(n_replicas=0), "n_replicas"),
     (dict(sweep_kernel=7), "sweep_kernel"),
+    (dict(band_rows=-1), "band_rows"),
+    (dict(band_rows=8, sweep_kernel=1), "band_rows"),
 ])
 def test_invalid_configs_rejected_on_host(lib, kw, msg):
     c, keep = _cfg(**kw)
