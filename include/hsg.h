@@ -111,6 +111,14 @@ typedef struct {
   int band_rows;          /* fused sweep: rows per CTA band, 0 = library choice;
                              otherwise L or a divisor of L >= 8 that fits the
                              block and shared-memory limits (HSG_EINVAL if not) */
+  int persistent;         /* 1: hsg_run_steps keeps every replica set (the N_T
+                             lattices of one replica of one sample) resident in
+                             shared memory and runs whole steps, PT included,
+                             in one launch per stretch of steps between
+                             measurements; needs N_T <= 64, N_T a multiple of
+                             the layout's lattices per element, and
+                             12 N_T L^3 bytes <= 224 KiB for every L
+                             (HSG_EINVAL otherwise).  0: streaming steps. */
 } hsg_config;
 
 /* Create a context: validates cfg (copied; the caller's arrays may be freed

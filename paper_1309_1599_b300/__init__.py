@@ -50,7 +50,7 @@ class _Config(ctypes.Structure):
                 ("layout", ctypes.c_int), ("n_or", ctypes.c_int), ("measure_every", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int),
-                ("band_rows", ctypes.c_int)]
+                ("band_rows", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 _SIGNATURES = {
@@ -145,7 +145,7 @@ class Lattice:
 
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
-                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0):
+                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0, persistent=False):
         lib = load_library()
         _require_gpu()
         if np.isscalar(L):
@@ -174,6 +174,7 @@ class Lattice:
         cfg.timeout_cycles = int(timeout_cycles)
         cfg.sweep_kernel = int(sweep_kernel)
         cfg.band_rows = int(band_rows)
+        cfg.persistent = 1 if persistent else 0
         h = ctypes.c_void_p()
         _check(lib.hsg_lattice_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -16,6 +16,7 @@
 
 #include "../../include/hsg.h"
 #include "fused.cuh"
+#include "persistent.cuh"
 #include "kernels.cuh"
 
 using namespace hsg;
@@ -86,6 +87,8 @@ struct hsg_ctx {
   cudaGraphExec_t g_step[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   uint64_t g_step_launches[2][2] = {{0, 0}, {0, 0}};  // kernels per graph replay
   int* d_status = nullptr;     // device status word (HSG_ETIMEOUT from bounded waits)
+  bool persistent = false;     // run_steps keeps replica sets resident in shared memory
+  size_t persistent_smem = 0;
   long long timeout_cycles = 0;
   int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
@@ -334,6 +337,65 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
   return false;
 }
 
+template <int V, int PREC>
+hsg_status allow_persistent_smem_one(size_t bytes) {
+  HSG_CUDA(cudaFuncSetAttribute(k_persistent<V, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(bytes)));
+  return HSG_OK;
+}
+
+hsg_status allow_persistent_smem(int V, int prec, size_t bytes) {
+  if (V == 2) return prec == HSG_F16 ? allow_persistent_smem_one<2, kPrecF16>(bytes)
+                                     : allow_persistent_smem_one<2, kPrecF32>(bytes);
+  return prec == HSG_F16 ? allow_persistent_smem_one<1, kPrecF16>(bytes)
+                         : allow_persistent_smem_one<1, kPrecF32>(bytes);
+}
+
+hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st);
+
+// `steps` whole Monte Carlo steps with every replica set resident in shared
+// memory: one launch over all buckets, then the sweep counters advance.
+hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
+  PersistentParams p;
+  if (h->buckets.size() > static_cast<size_t>(kMaxBuckets)) return fail(HSG_EINVAL, "too many distinct L");
+  int ctas = 0;
+  p.n_buckets = static_cast<int>(h->buckets.size());
+  for (size_t j = 0; j < h->buckets.size(); ++j) {
+    const Bucket& b = h->buckets[j];
+    p.b[j].spins = b.d_spins[b.cur];
+    p.b[j].J = b.d_J;
+    p.b[j].sample_ids = b.d_samples;
+    p.b[j].L = b.L;
+    p.b[j].N = b.N;
+    p.b[j].S_b = b.S_b;
+    p.b[j].G = b.G;
+    p.b[j].cta_begin = ctas;
+    ctas += b.S_b * h->n_rep;
+  }
+  p.R = h->R;
+  p.n_rep = h->n_rep;
+  p.NT = h->NT;
+  p.n_or = h->n_or;
+  p.steps = steps;
+  p.beta = h->d_beta;
+  p.E = h->d_E;
+  p.perm = h->d_perm;
+  p.temp_of = h->d_temp_of;
+  p.accepted = h->d_pt_acc;
+  p.key = philox_key(h->seed);
+  p.counters = h->d_counters;
+  *h->launch_sink += 1;
+  if (h->V == 2) {
+    if (h->prec == HSG_F16) k_persistent<2, kPrecF16><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
+    else k_persistent<2, kPrecF32><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
+  } else {
+    if (h->prec == HSG_F16) k_persistent<1, kPrecF16><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
+    else k_persistent<1, kPrecF32><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
+  }
+  HSG_CUDA(cudaGetLastError());
+  return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
+}
+
 hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st) {
   *h->launch_sink += 1;
   k_bump_counters<<<1, 1, 0, st>>>(h->d_counters, dhb, dpt);
@@ -524,6 +586,17 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     return fail(HSG_EINVAL, "sweep_kernel must be HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS");
   if (cfg->band_rows < 0 || (cfg->band_rows > 0 && cfg->sweep_kernel != HSG_SWEEP_AUTO))
     return fail(HSG_EINVAL, "band_rows must be 0, or > 0 with the fused sweep");
+  if (cfg->persistent != 0 && cfg->persistent != 1) return fail(HSG_EINVAL, "persistent must be 0 or 1");
+  if (cfg->persistent) {
+    if (cfg->n_temps > kMaxTempsResident) return fail(HSG_EINVAL, "persistent steps need n_temps <= 64");
+    if (cfg->layout == HSG_LAYOUT_BATCHED && cfg->n_temps % 2 != 0)
+      return fail(HSG_EINVAL, "persistent steps need n_temps to be a multiple of the lattices per element");
+    for (int s = 0; s < cfg->n_samples; ++s) {
+      const size_t Ls = cfg->L[s];
+      if (12 * static_cast<size_t>(cfg->n_temps) * Ls * Ls * Ls > 224 * 1024)
+        return fail(HSG_EINVAL, "a replica set (12 n_temps L^3 bytes) does not fit in shared memory");
+    }
+  }
   for (int s = 0; s < cfg->n_samples; ++s) {
     const int L = cfg->L[s];
     if (L < 4 || L > 512 || (L & 1)) return fail(HSG_EINVAL, "each L must be even and in [4, 512]");
@@ -553,6 +626,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   h->stream = static_cast<cudaStream_t>(cfg->stream);
   h->timeout_cycles = cfg->timeout_cycles > 0 ? cfg->timeout_cycles : 4000000000LL;
   h->sweep_kernel = cfg->sweep_kernel;
+  h->persistent = cfg->persistent != 0;
   h->launch_sink = &h->launches;
   h->Ls.assign(cfg->L, cfg->L + cfg->n_samples);
   h->beta.assign(cfg->beta, cfg->beta + cfg->n_temps);
@@ -642,6 +716,11 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   }
 
   if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
+  if (h->persistent) {
+    for (const Bucket& b : h->buckets)
+      h->persistent_smem = std::max(h->persistent_smem, static_cast<size_t>(12) * h->NT * b.N);
+    if (allow_persistent_smem(V, h->prec, h->persistent_smem) != HSG_OK) return bail(HSG_ECUDA);
+  }
   const size_t S = h->S, NT = h->NT;
   hsg_status st;
   if ((st = dalloc(&h->d_perm, S * h->n_rep * NT)) != HSG_OK) return bail(st);
@@ -895,6 +974,25 @@ hsg_status hsg_measure(hsg_t h) {
 hsg_status hsg_run_steps(hsg_t h, int n_steps) {
   if (!h || n_steps < 0) return fail(HSG_EINVAL, "bad handle or n_steps < 0");
   if (n_steps == 0) return HSG_OK;
+  if (h->persistent) {
+    int left = n_steps;
+    while (left > 0) {
+      int k = left;
+      if (h->measure_every > 0) {
+        const uint64_t m = static_cast<uint64_t>(h->measure_every);
+        k = static_cast<int>(std::min<uint64_t>(k, m - h->counters[2] % m));
+      }
+      HSG_TRY(enqueue_persistent(h, k, h->stream));
+      h->counters[0] += k;
+      h->counters[1] += k;
+      h->counters[2] += k;
+      left -= k;
+      if (h->measure_every > 0 && h->counters[2] % static_cast<uint64_t>(h->measure_every) == 0)
+        HSG_TRY(enqueue_measure(h, h->stream));
+    }
+    h->energy_valid = true;
+    return HSG_OK;
+  }
   // sweeps per step: one heat-bath sweep plus n_or overrelaxation sweeps;
   // each fused sweep flips the buffer index
   const int flips = (1 + h->n_or) & 1;

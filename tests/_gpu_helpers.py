@@ -17,12 +17,12 @@ FRAME_EPS = 1e-4
 
 
 def make(Ls, beta, n_rep=2, prec=hsg.F32, layout=hsg.PLAIN, n_or=8, measure_every=0,
-         seed=SEED, law="gaussian"):
+         seed=SEED, law="gaussian", persistent=False):
     """Context with couplings and random spins from hsg_inputs; returns
     (lattice, couplings per sample as stored, float32 [N,3,6])."""
     Ls = [Ls] if np.isscalar(Ls) else list(Ls)
     lat = hsg.Lattice(Ls, beta, n_replicas=n_rep, coupling_prec=prec, layout=layout,
-                      n_or=n_or, measure_every=measure_every, seed=seed)
+                      n_or=n_or, measure_every=measure_every, seed=seed, persistent=persistent)
     pstr = "f16" if prec == hsg.F16 else "f32"
     J = []
     for s, L in enumerate(Ls):

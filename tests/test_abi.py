@@ -52,6 +52,7 @@ def _cfg(**kw):
     c.timeout_cycles = 0
     c.sweep_kernel = kw.pop("sweep_kernel", 0)
     c.band_rows = kw.pop("band_rows", 0)
+    c.persistent = kw.pop("persistent", 0)
     return c, (L, beta)
 
 
@@ -64,6 +65,8 @@ def _cfg(**kw):
     (dict(sweep_kernel=7), "sweep_kernel"),
     (dict(band_rows=-1), "band_rows"),
     (dict(band_rows=8, sweep_kernel=1), "band_rows"),
+    (dict(L=32, persistent=1), "shared memory"),
+    (dict(persistent=1, layout=1, beta=[1.0, 2.0, 3.0], n_replicas=2), "multiple"),
 ])
 def test_invalid_configs_rejected_on_host(lib, kw, msg):
     c, keep = _cfg(**kw)

@@ -1,0 +1,67 @@
+"""Shared-memory-resident steps (the whole Monte Carlo step of Sec. III in one
+launch per stretch of steps) against the streaming path and the oracle."""
+import numpy as np
+import pytest
+
+import hsg_inputs as gi
+import oracle
+import paper_1309_1599_b300 as hsg
+from _gpu_helpers import make, state
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # Ls, n_temps, n_rep, prec, layout, n_or, measure_every, steps
+    ([8, 12], 8, 2, hsg.F16, hsg.BATCHED, 3, 2, 6),
+    ([12, 8, 8], 4, 3, hsg.F32, hsg.PLAIN, 8, 3, 7),
+    ([10], 6, 2, hsg.F32, hsg.BATCHED, 2, 0, 5),
+    ([8], 1, 2, hsg.F16, hsg.PLAIN, 1, 1, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"L{'-'.join(map(str, c[0]))}_T{c[1]}")
+def test_persistent_steps_equal_streaming_steps(case):
+    """Same spins bit for bit, same labels and acceptances, energies and
+    observables equal up to the summation order of the energies."""
+    Ls, NT, n_rep, prec, layout, n_or, me, steps = case
+    betas = gi.linear_betas(0.2, 1.2, NT)
+    a, _ = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout, n_or=n_or, measure_every=me)
+    b, _ = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout, n_or=n_or, measure_every=me,
+                persistent=True)
+    a.run_steps(steps - 2)
+    a.run_steps(2)
+    b.run_steps(steps - 2)
+    b.run_steps(2)
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.get_perm(), b.get_perm())
+    assert np.array_equal(a.get_pt_accepts(), b.get_pt_accepts())
+    assert np.array_equal(a.get_counters(), b.get_counters())
+    Ea, Eb = a.get_energies(), b.get_energies()
+    assert np.allclose(Ea, Eb, rtol=1e-9, atol=1e-9 * np.abs(Ea).max()), np.abs(Ea - Eb).max()
+    oa, ca = a.read_observables()
+    ob, cb = b.read_observables()
+    assert np.array_equal(ca, cb)
+    if me:
+        assert ca.min() == steps // me
+    assert np.allclose(oa, ob, rtol=1e-9, atol=1e-12)
+    # one launch per stretch of steps between measurements (+ counter bump)
+    assert b.get_launch_count() < a.get_launch_count()
+
+
+def test_persistent_step_matches_oracle_steps():
+    """Three whole steps (HB + 8 OR + energies + PT) from the initial state:
+    labels identical to the oracle's, spins within the per-sweep tolerance
+    accumulated over the 27 sweeps."""
+    betas = gi.linear_betas(0.5, 1.0, 4)
+    lat, J = make([8], betas, n_rep=2, prec=hsg.F32, layout=hsg.BATCHED, persistent=True)
+    st = state(lat)
+    smp = oracle.Sample(8, J[0], np.stack(st[0]), betas, 2, lat.seed)
+    lat.run_steps(3)
+    smp.run(3, 8, 0)
+    assert np.array_equal(lat.get_perm().reshape(-1), smp.perm)
+    d = max(np.abs(lat.get_spins(0, j) - smp.spins[j]).max() for j in range(lat.R))
+    assert d < 1e-3, d
+    E = lat.get_energies()[0]
+    for j in range(lat.R):
+        ref = oracle.energy(8, oracle.j9_from_j6(J[0]), lat.get_spins(0, j).astype(np.float64))
+        assert abs(E[j] - ref) <= 2e-6 * abs(ref)
