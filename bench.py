@@ -46,6 +46,10 @@ WORKLOADS = {
     # profiling size of the L=64 tiling: one sample, 64 lattices (201 MB of spins)
     "L64_S1_R64_f16": dict(L=64, S=1, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
+    # many small lattices of mixed L, every replica set resident in shared
+    # memory (4 replicas x 8 temperatures per sample)
+    "L8x256_L12x256_R32_f16": dict(Ls=(8,) * 256 + (12,) * 256, S=512, n_rep=4, NT=8, Tmin=0.2,
+                                   Tmax=0.8, n_or=8, measure_every=10, persistent=True),
 }
 DEFAULT_WORKLOAD = "L64_S8_R64_f16"
 
@@ -57,9 +61,14 @@ NCU_TRAFFIC = {
 }
 
 
+def sample_Ls(w):
+    """Linear size of each sample of the workload."""
+    return list(w["Ls"]) if "Ls" in w else [w["L"]] * w["S"]
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "fused.cuh", "philox.cuh", "hsg.cu"):
+    for f in ("kernels.cuh", "fused.cuh", "persistent.cuh", "philox.cuh", "hsg.cu"):
         with open(os.path.join(ROOT, "paper_1309_1599_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -72,6 +81,20 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+# Peak of the FP32 pipe: 148 SMs x 128 FP32 lanes x 2 flops (FMA) x 2032 MHz.
+ALU_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# Algorithmic FP32 flops per site update: the local field is 18 FMA per bond
+# direction pair (6 3x3 matrix-vector products = 54 FMA = 108 flops); an
+# overrelaxation adds h.h, h.s, the ratio and s' = c h - s (20 flops), a
+# heat-bath draw the kappa, inverse-CDF and rotation arithmetic (40 flops,
+# transcendentals counted once each).
+FLOPS_OR, FLOPS_HB = 128, 148
+
+
+def flops_per_update(n_or: int) -> float:
+    return (FLOPS_HB + n_or * FLOPS_OR) / (1 + n_or)
 
 
 def b_alg(R_share: int, bond_bytes: int) -> float:
@@ -124,10 +147,10 @@ class Dist:
 # ----------------------------------------------------------------------------
 def make_inputs(w, rank, seed=1):
     import hsg_inputs as gi
-    L, S, R = w["L"], w["S"], w["n_rep"] * w["NT"]
+    Ls, S, R = sample_Ls(w), w["S"], w["n_rep"] * w["NT"]
     samples = [rank * S + s for s in range(S)]
-    J = [gi.couplings(L, seed, sg, precision="f16") for sg in samples]
-    spins = [[gi.random_spins(L, seed, sg, j) for j in range(R)] for sg in samples]
+    J = [gi.couplings(Ls[s], seed, sg, precision="f16") for s, sg in enumerate(samples)]
+    spins = [[gi.random_spins(Ls[s], seed, sg, j) for j in range(R)] for s, sg in enumerate(samples)]
     beta = gi.linear_betas(w["Tmin"], w["Tmax"], w["NT"])
     return samples, J, spins, beta
 
@@ -185,10 +208,11 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # the hsg arm
 # ----------------------------------------------------------------------------
-def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0):
-    lat = hsg.Lattice([w["L"]] * len(samples), beta, n_replicas=w["n_rep"], coupling_prec=prec,
+def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0,
+                  persistent=False):
+    lat = hsg.Lattice(sample_Ls(w), beta, n_replicas=w["n_rep"], coupling_prec=prec,
                       layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed,
-                      band_rows=band_rows)
+                      band_rows=band_rows, persistent=persistent)
     for s in range(len(samples)):
         lat.set_couplings(s, J[s])
         for j in range(lat.R):
@@ -236,24 +260,66 @@ def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
     return e0.elapsed_time(e1) / (n_calls * per_sweep * sweeps)
 
 
-def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0):
+def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3):
+    """Average duration of one launch of the resident-step kernel (10 whole
+    MCS, no measurement) from CUDA events on the library's stream."""
     samples, J, spins, beta = inputs
-    lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows)
-    N, R, S = w["L"] ** 3, lat.R, len(samples)
+    wk = dict(w, measure_every=0)
+    lat = build_lattice(hsg, wk, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=True)
+    stream = torch.cuda.current_stream()
+    lat.run_steps(MCS_PER_STEP)
+    torch.cuda.synchronize()
+    l0 = lat.get_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_calls):
+        lat.run_steps(MCS_PER_STEP)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    # each call: one resident-step launch + one counter bump (~2 us)
+    assert lat.get_launch_count() - l0 == 2 * n_calls
+    lat.destroy()
+    return e0.elapsed_time(e1) / n_calls
+
+
+def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0,
+             persistent=False):
+    samples, J, spins, beta = inputs
+    lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows,
+                        persistent=persistent)
+    R = lat.R
+    n_sites = sum(L ** 3 for L in sample_Ls(w))
     for _ in range(warmup):
         lat.run_steps(MCS_PER_STEP)
     torch.cuda.synchronize()
     ms, launches, clocks = time_steps(lat, steps, torch, dist, sampler)
     ms_max = dist.max(ms)
-    updates_rank = S * R * N * (1 + w["n_or"]) * MCS_PER_STEP * steps
+    updates_rank = R * n_sites * (1 + w["n_or"]) * MCS_PER_STEP * steps
     value = updates_rank * dist.world / (ms_max * 1e6)
+    if persistent:
+        lat.destroy()
+        k_ms = time_persistent_kernel(hsg, w, inputs, torch)
+        upd = R * n_sites * (1 + w["n_or"]) * MCS_PER_STEP
+        fpu = flops_per_update(w["n_or"])
+        achieved = upd * fpu / (k_ms * 1e-3) / 1e12
+        vname = 2 if layout == hsg.BATCHED else 1
+        roof = {"bound": "alu", "kernel": f"k_persistent<{vname},f16> ({MCS_PER_STEP} MCS per launch)",
+                "achieved": round(achieved, 2), "peak": round(ALU_PEAK_TFLOPS, 2),
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
+                "unit": "TFLOP/s", "frac": round(achieved / ALU_PEAK_TFLOPS, 4),
+                "flops_per_update": round(fpu, 2), "launch_ms": round(k_ms, 4),
+                "updates_per_ns_kernel": round(upd / (k_ms * 1e6), 2),
+                "traffic": None}
+        return dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
+                    roofline=roof, lat=None)
     or_ms = time_or_kernel(lat, torch)
     bond_bytes = 12 if prec == hsg.F16 else 24
     r_share = R if layout == hsg.BATCHED else 1
     balg = b_alg(r_share, bond_bytes)
     plan = lat.get_sweep_plan(0)
     # updates per launch: every site (fused sweep) or half of them (half-sweep)
-    upd_launch = S * R * N // plan["launches_per_sweep"]
+    upd_launch = R * n_sites // plan["launches_per_sweep"]
     bytes_launch = upd_launch * balg
     achieved = bytes_launch / (or_ms * 1e-3) / 1e9
     vname = 2 if layout == hsg.BATCHED else 1
@@ -280,15 +346,16 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     initial spins host->device, `steps` bench steps, observables and final
     spins device->host.  Wall time around it, synchronised."""
     samples, J, spins, beta = inputs
-    L, S = w["L"], len(samples)
-    lat = hsg.Lattice([L] * S, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
-                      layout=hsg.BATCHED, n_or=w["n_or"], measure_every=w["measure_every"])
-    R, N = lat.R, L ** 3
+    Ls, S = sample_Ls(w), len(samples)
+    lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
+                      layout=hsg.BATCHED, n_or=w["n_or"], measure_every=w["measure_every"],
+                      persistent=w.get("persistent", False))
+    R, n_sites = lat.R, sum(L ** 3 for L in Ls)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     J_h = [pin(j) for j in J]
     s_h = [[pin(x) for x in row] for row in spins]
-    out_h = [[torch.empty((N, 3), dtype=torch.float32).pin_memory() for _ in range(R)]
-             for _ in range(S)]
+    out_h = [[torch.empty((Ls[s] ** 3, 3), dtype=torch.float32).pin_memory() for _ in range(R)]
+             for s in range(S)]
     lat.run_steps(1)                   # capture graphs outside the timed region
     torch.cuda.synchronize()
     dist.barrier()
@@ -306,9 +373,9 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     torch.cuda.synchronize()
     dt = dist.max(time.perf_counter() - t0)
     lat.destroy()
-    updates = S * R * N * (1 + w["n_or"]) * MCS_PER_STEP * steps * dist.world
-    h2d = sum(x.numel() * 4 for x in J_h) + S * R * N * 12
-    d2h = obs.nbytes + counts.nbytes + S * R * N * 12
+    updates = R * n_sites * (1 + w["n_or"]) * MCS_PER_STEP * steps * dist.world
+    h2d = sum(x.numel() * 4 for x in J_h) + R * n_sites * 12
+    d2h = obs.nbytes + counts.nbytes + R * n_sites * 12
     return {"value": updates / (dt * 1e9), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
             "wall_s": round(dt, 3)}
@@ -322,24 +389,25 @@ def oracle_sample_run(w, inputs, n_mcs, threads):
     Monte Carlo steps; returns (updates, seconds)."""
     import oracle
     samples, J, spins, beta = inputs
-    smp = oracle.Sample(w["L"], J[0], np.stack(spins[0]), beta, w["n_rep"], 1,
+    L = sample_Ls(w)[0]
+    smp = oracle.Sample(L, J[0], np.stack(spins[0]), beta, w["n_rep"], 1,
                         sample_index=samples[0])
     t0 = time.perf_counter()
     smp.run(n_mcs, w["n_or"], w["measure_every"], n_threads=threads)
     dt = time.perf_counter() - t0
-    return smp.R * w["L"] ** 3 * (1 + w["n_or"]) * n_mcs, dt
+    return smp.R * L ** 3 * (1 + w["n_or"]) * n_mcs, dt
 
 
 def cpu_baseline(w, inputs, budget_s=15.0):
     threads = os.cpu_count() or 1
     ups, dt = oracle_sample_run(w, inputs, 1, threads)
     n = 1
-    while dt < budget_s / 3 and n < 64:
+    while dt < budget_s / 3 and n < 4096:
         more = max(1, int(n * (budget_s / max(dt, 1e-3) - 1)))
         u2, d2 = oracle_sample_run(w, inputs, more, threads)
         ups, dt, n = ups + u2, dt + d2, n + more
     return {"value": ups / (dt * 1e9), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} MCS of 1 sample ({w['n_rep'] * w['NT']} lattices of L={w['L']}, "
+            "sample": f"{n} MCS of 1 sample ({w['n_rep'] * w['NT']} lattices of L={sample_Ls(w)[0]}, "
                       f"FP16-quantised couplings as FP64), OpenMP over lattices, "
                       f"{dt:.1f} s"}
 
@@ -363,7 +431,8 @@ def reference_arm(args, w, world, rank, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "step": "1 MCS of 1 sample (bounded CPU sample)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
-                             "sample": "each step: 1 MCS of sample 0 (64 lattices of L=64)"},
+                             "sample": f"each step: 1 MCS of sample 0 ({w['n_rep'] * w['NT']} lattices "
+                                       f"of L={sample_Ls(w)[0]})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -395,11 +464,19 @@ def main():
     inputs = make_inputs(w, rank)
 
     sampler = ClockSampler(local)
+    persistent = w.get("persistent", False)
     batched = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
-                       args.warmup, sampler, peak, band_rows=args.band_rows)
-    batched["lat"].destroy()
+                       args.warmup, sampler, peak, band_rows=args.band_rows, persistent=persistent)
+    if batched["lat"] is not None:
+        batched["lat"].destroy()
+    streaming = None
+    if persistent:
+        # the same workload through the streaming kernels, for comparison
+        streaming = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
+                             args.warmup, None, peak)
+        streaming["lat"].destroy()
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and not persistent:
         plain = run_form(hsg, torch, dist, w, inputs, hsg.F32, hsg.PLAIN, args.steps,
                          args.warmup, None, peak)
         plain["lat"].destroy()
@@ -412,12 +489,17 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(batched["ms_per_step"], 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "L": w["L"], "samples_per_gpu": w["S"],
+                "config": {"workload": args.workload,
+                           "L": w["L"] if "L" in w else sorted(set(sample_Ls(w))),
+                           "samples_per_gpu": w["S"],
                            "lattices_per_sample": w["n_rep"] * w["NT"], "n_temps": w["NT"],
                            "T_range": [w["Tmin"], w["Tmax"]], "n_or": w["n_or"],
                            "couplings": "gaussian, FP16-quantised", "layout": "batched",
                            "step": f"{MCS_PER_STEP} MCS (HB + {w['n_or']} OR + PT each) + 1 measurement",
-                           "l2": "no flush: spins per GPU exceed L2 (126 MB)",
+                           "l2": ("no flush: spins per GPU exceed L2 (126 MB)" if not persistent else
+                                  "no flush: spins stay in shared memory within a launch; "
+                                  "the whole set (220 MB per GPU) exceeds L2"),
+                           "resident": persistent,
                            "parallelism": f"replicas x{world} (independent samples per GPU)"},
                 "roofline": batched["roofline"], "gpu_launches": batched["launches"],
                 "clocks": batched["clocks"], "e2e": e2e, "cpu_baseline": cpu}
@@ -426,6 +508,12 @@ def main():
                                   "ms_per_step": round(plain["ms_per_step"], 3),
                                   "roofline": plain["roofline"], "gpu_launches": plain["launches"]}
             line["batched_over_plain"] = round(batched["value"] / plain["value"], 3)
+        if streaming is not None:
+            line["streaming_f16"] = {"value": round(streaming["value"], 3),
+                                     "ms_per_step": round(streaming["ms_per_step"], 3),
+                                     "roofline": streaming["roofline"],
+                                     "gpu_launches": streaming["launches"]}
+            line["resident_over_streaming"] = round(batched["value"] / streaming["value"], 3)
         print(json.dumps(line), flush=True)
     dist.close()
     return 0

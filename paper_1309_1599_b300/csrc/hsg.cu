@@ -977,7 +977,8 @@ hsg_status hsg_run_steps(hsg_t h, int n_steps) {
   if (h->persistent) {
     int left = n_steps;
     while (left > 0) {
-      int k = left;
+      // bounded launches: at most kMaxStepsPerLaunch steps each
+      int k = std::min(left, kMaxStepsPerLaunch);
       if (h->measure_every > 0) {
         const uint64_t m = static_cast<uint64_t>(h->measure_every);
         k = static_cast<int>(std::min<uint64_t>(k, m - h->counters[2] % m));

@@ -27,6 +27,7 @@ namespace hsg {
 constexpr int kPersistentThreads = 512;
 constexpr int kMaxBuckets = 8;
 constexpr int kMaxTempsResident = 64;
+constexpr int kMaxStepsPerLaunch = 256;
 
 struct PersistentBucket {
   float* spins;            // bucket spins [S_b][G][3][N][V]

