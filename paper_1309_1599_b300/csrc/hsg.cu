@@ -52,6 +52,8 @@ struct Bucket {
   int m_chunks = 0, P = 0;
   double* d_mpart = nullptr;  // [S_b][NT][P][m_chunks][kNQ]
   float* d_phase = nullptr;   // [L][2]
+  bool res_js = false;        // resident steps: bonds resident in shared memory too
+  size_t res_smem = 0;        // resident steps: dynamic shared memory per CTA
 };
 
 }  // namespace
@@ -88,7 +90,6 @@ struct hsg_ctx {
   uint64_t g_step_launches[2][2] = {{0, 0}, {0, 0}};  // kernels per graph replay
   int* d_status = nullptr;     // device status word (HSG_ETIMEOUT from bounded waits)
   bool persistent = false;     // run_steps keeps replica sets resident in shared memory
-  size_t persistent_smem = 0;
   long long timeout_cycles = 0;
   int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
@@ -337,62 +338,77 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
   return false;
 }
 
-template <int V, int PREC>
-hsg_status allow_persistent_smem_one(size_t bytes) {
-  HSG_CUDA(cudaFuncSetAttribute(k_persistent<V, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(bytes)));
-  return HSG_OK;
+// Resident-step kernel for (V, precision, bonds resident).
+template <int V, int PREC, bool JS>
+void* persistent_fn() {
+  return reinterpret_cast<void*>(k_persistent<V, PREC, JS>);
 }
 
-hsg_status allow_persistent_smem(int V, int prec, size_t bytes) {
-  if (V == 2) return prec == HSG_F16 ? allow_persistent_smem_one<2, kPrecF16>(bytes)
-                                     : allow_persistent_smem_one<2, kPrecF32>(bytes);
-  return prec == HSG_F16 ? allow_persistent_smem_one<1, kPrecF16>(bytes)
-                         : allow_persistent_smem_one<1, kPrecF32>(bytes);
+void* persistent_kernel(int V, int prec, bool js) {
+  if (V == 2) {
+    if (prec == HSG_F16) return js ? persistent_fn<2, kPrecF16, true>() : persistent_fn<2, kPrecF16, false>();
+    return js ? persistent_fn<2, kPrecF32, true>() : persistent_fn<2, kPrecF32, false>();
+  }
+  if (prec == HSG_F16) return js ? persistent_fn<1, kPrecF16, true>() : persistent_fn<1, kPrecF16, false>();
+  return js ? persistent_fn<1, kPrecF32, true>() : persistent_fn<1, kPrecF32, false>();
+}
+
+// Plans the resident steps of every bucket: spins 12 N_T N bytes, plus the
+// bonds (3 N per sample) when both fit in the block's shared memory; sets the
+// kernels' dynamic shared-memory limits.
+hsg_status plan_persistent(hsg_ctx* h) {
+  int dev = 0, optin = 0;
+  HSG_CUDA(cudaGetDevice(&dev));
+  HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  size_t need[2] = {0, 0};
+  for (Bucket& b : h->buckets) {
+    cudaFuncAttributes fa;
+    HSG_CUDA(cudaFuncGetAttributes(&fa, persistent_kernel(h->V, h->prec, true)));
+    const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+    const size_t spins = static_cast<size_t>(12) * h->NT * b.N;
+    const size_t bonds = static_cast<size_t>(3) * b.N * (h->prec == HSG_F16 ? 12 : 24);
+    if (spins > budget) return fail(HSG_EINVAL, "a replica set does not fit in shared memory");
+    b.res_js = spins + bonds <= budget;
+    b.res_smem = b.res_js ? spins + bonds : spins;
+    need[b.res_js] = std::max(need[b.res_js], b.res_smem);
+  }
+  for (int js = 0; js < 2; ++js)
+    if (need[js] > 0)
+      HSG_CUDA(cudaFuncSetAttribute(persistent_kernel(h->V, h->prec, js != 0),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(need[js])));
+  return HSG_OK;
 }
 
 hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st);
 
 // `steps` whole Monte Carlo steps with every replica set resident in shared
-// memory: one launch over all buckets, then the sweep counters advance.
+// memory: one launch per bucket, then the sweep counters advance.
 hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
-  PersistentParams p;
-  if (h->buckets.size() > static_cast<size_t>(kMaxBuckets)) return fail(HSG_EINVAL, "too many distinct L");
-  int ctas = 0;
-  p.n_buckets = static_cast<int>(h->buckets.size());
-  for (size_t j = 0; j < h->buckets.size(); ++j) {
-    const Bucket& b = h->buckets[j];
-    p.b[j].spins = b.d_spins[b.cur];
-    p.b[j].J = b.d_J;
-    p.b[j].sample_ids = b.d_samples;
-    p.b[j].L = b.L;
-    p.b[j].N = b.N;
-    p.b[j].S_b = b.S_b;
-    p.b[j].G = b.G;
-    p.b[j].cta_begin = ctas;
-    ctas += b.S_b * h->n_rep;
+  for (const Bucket& b : h->buckets) {
+    PersistentParams p;
+    p.spins = b.d_spins[b.cur];
+    p.J = b.d_J;
+    p.sample_ids = b.d_samples;
+    p.L = b.L;
+    p.N = b.N;
+    p.G = b.G;
+    p.R = h->R;
+    p.n_rep = h->n_rep;
+    p.NT = h->NT;
+    p.n_or = h->n_or;
+    p.steps = steps;
+    p.beta = h->d_beta;
+    p.E = h->d_E;
+    p.perm = h->d_perm;
+    p.temp_of = h->d_temp_of;
+    p.accepted = h->d_pt_acc;
+    p.key = philox_key(h->seed);
+    p.counters = h->d_counters;
+    void* args[] = {&p};
+    *h->launch_sink += 1;
+    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js), dim3(b.S_b * h->n_rep),
+                              dim3(kPersistentThreads), args, b.res_smem, st));
   }
-  p.R = h->R;
-  p.n_rep = h->n_rep;
-  p.NT = h->NT;
-  p.n_or = h->n_or;
-  p.steps = steps;
-  p.beta = h->d_beta;
-  p.E = h->d_E;
-  p.perm = h->d_perm;
-  p.temp_of = h->d_temp_of;
-  p.accepted = h->d_pt_acc;
-  p.key = philox_key(h->seed);
-  p.counters = h->d_counters;
-  *h->launch_sink += 1;
-  if (h->V == 2) {
-    if (h->prec == HSG_F16) k_persistent<2, kPrecF16><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
-    else k_persistent<2, kPrecF32><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
-  } else {
-    if (h->prec == HSG_F16) k_persistent<1, kPrecF16><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
-    else k_persistent<1, kPrecF32><<<ctas, kPersistentThreads, h->persistent_smem, st>>>(p);
-  }
-  HSG_CUDA(cudaGetLastError());
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }
 
@@ -717,9 +733,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
 
   if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
   if (h->persistent) {
-    for (const Bucket& b : h->buckets)
-      h->persistent_smem = std::max(h->persistent_smem, static_cast<size_t>(12) * h->NT * b.N);
-    if (allow_persistent_smem(V, h->prec, h->persistent_smem) != HSG_OK) return bail(HSG_ECUDA);
+    const hsg_status ps = plan_persistent(h);
+    if (ps != HSG_OK) return bail(ps);
   }
   const size_t S = h->S, NT = h->NT;
   hsg_status st;

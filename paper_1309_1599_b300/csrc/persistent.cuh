@@ -1,45 +1,46 @@
 // Shared-memory-resident Monte Carlo of small lattices: one launch runs K
 // whole Monte Carlo steps (Sec. III: heat-bath sweep, overrelaxation sweeps,
-// energies, one parallel-tempering sweep) for every replica set of every
-// sample, with the spins of a replica set held in shared memory from the
-// first step to the last.
+// energies, one parallel-tempering sweep) for every replica set of the
+// samples of one L, with the spins of a replica set held in shared memory
+// from the first step to the last.
 //
 // A CTA owns one replica set: the N_T lattices of one replica index of one
-// sample (all temperatures), V lattices interleaved per element exactly as in
-// global memory, so the set is one contiguous block copied in at the start
-// and out at the end.  Parallel tempering only exchanges temperatures inside
-// a replica set (App. A.1), so each CTA runs its own PT sweep after its own
-// energies; no CTA ever waits for another.  Samples of different L (buckets)
-// run in the same launch; a CTA finds its bucket from its index.
+// sample (all temperatures).  Parallel tempering only exchanges temperatures
+// inside a replica set (App. A.1), so each CTA runs its own PT sweep after its
+// own energies; no CTA ever waits for another.
 //
-// The arithmetic is that of the streaming kernels: the same site order, the
-// same field summation (forward and backward partial sums), the same
-// single-spin updates and the same Philox counters (the sweep counters
-// advance by one per step), so the spins agree bit for bit with the
-// streaming path as long as the PT decisions agree (their energies are
-// summed in a different order, so a decision within rounding of its
-// threshold may differ).
+// Shared-memory layout.  Global memory keeps each row's sites split by x
+// parity (the streaming kernels' order).  In shared memory the sites are split
+// by colour instead: colour c holds its N/2 sites in (row, x>>1) order, so
+// the sites a warp updates and each of their six neighbours are consecutive
+// words and the accesses are free of bank conflicts:
+//   spins  [G_set][3][2 colours][N/2][V] floats
+//   bonds  [3 directions][2 colours][N/2] x 6 entries (FP16: 12 B, FP32: 24 B),
+//          the bond (x, x+mu) stored at its lower site x, when they fit
+//          beside the spins (JS); otherwise read from global memory.
+//
+// The arithmetic is that of the streaming kernels: the same field summation
+// (forward and backward partial sums), the same single-spin updates and the
+// same Philox counters (the sweep counters advance by one per step), so the
+// spins agree bit for bit with the streaming path as long as the PT
+// decisions agree (their energies are summed in a different order, so a
+// decision within rounding of its threshold may differ).
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace hsg {
 
 constexpr int kPersistentThreads = 512;
-constexpr int kMaxBuckets = 8;
 constexpr int kMaxTempsResident = 64;
 constexpr int kMaxStepsPerLaunch = 256;
 
-struct PersistentBucket {
-  float* spins;            // bucket spins [S_b][G][3][N][V]
-  const void* J;           // bucket couplings
-  const int* sample_ids;   // [S_b]
-  int L, N, S_b, G;
-  int cta_begin;           // first CTA of this bucket (CTAs = S_b * n_rep)
-};
-
 struct PersistentParams {
-  PersistentBucket b[kMaxBuckets];
-  int n_buckets;
+  float* spins;            // bucket spins [S_b][G][3][N][V]
+  const void* J;           // bucket couplings (global storage order)
+  const int* sample_ids;   // [S_b]
+  int L, N, G;
   int R, n_rep, NT, n_or, steps;
   const double* beta;      // [NT]
   double* E;               // [S][R]
@@ -50,8 +51,12 @@ struct PersistentParams {
   const uint32_t* counters;  // [0] heat-bath sweeps, [1] PT sweeps (at launch)
 };
 
+// bytes of one bond (6 entries) in the resident layout
+template <int PREC>
+constexpr int resident_bond_bytes() { return PREC == kPrecF16 ? 12 : 24; }
+
 template <int V>
-__device__ __forceinline__ void lds_plane(const float* base, size_t plane, int i, float (&s)[3][V]) {
+__device__ __forceinline__ void lds_plane(const float* base, int plane, int i, float (&s)[3][V]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if constexpr (V == 2) {
@@ -65,7 +70,7 @@ __device__ __forceinline__ void lds_plane(const float* base, size_t plane, int i
 }
 
 template <int V>
-__device__ __forceinline__ void sts_plane(float* base, size_t plane, int i, const float (&s)[3][V]) {
+__device__ __forceinline__ void sts_plane(float* base, int plane, int i, const float (&s)[3][V]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if constexpr (V == 2) {
@@ -76,103 +81,153 @@ __device__ __forceinline__ void sts_plane(float* base, size_t plane, int i, cons
   }
 }
 
-// One colour half-sweep (KIND: heat-bath or overrelaxation) of the resident
-// replica set, sp: [G_set][3][N][V] in shared memory.  The (site, group)
-// pairs of the colour are spread over the threads, consecutive threads on
-// consecutive sites of one group.
-template <int KIND, int V, int PREC>
-__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Jb, int L, int N, int G_set, int colour,
-                                                    const float* beta_lat, uint32_t lat_base, uint32_t t,
-                                                    uint2 key) {
+// One bond from the resident layout: the same floats as load_bond() gives for
+// the same stored entries.
+template <int PREC>
+__device__ __forceinline__ void lds_bond(const void* Js, int idx, float (&j)[6]) {
+  if constexpr (PREC == kPrecF16) {
+    const uint32_t* p = static_cast<const uint32_t*>(Js) + 3 * idx;
+    __half2 h0, h1, h2;
+    *reinterpret_cast<uint32_t*>(&h0) = p[0];
+    *reinterpret_cast<uint32_t*>(&h1) = p[1];
+    *reinterpret_cast<uint32_t*>(&h2) = p[2];
+    const float2 a = __half22float2(h0), b = __half22float2(h1), c = __half22float2(h2);
+    j[0] = a.x; j[1] = a.y; j[2] = b.x; j[3] = b.y; j[4] = c.x; j[5] = c.y;
+  } else {
+    const float2* p = reinterpret_cast<const float2*>(static_cast<const float*>(Js) + 6 * idx);
+    const float2 a = p[0], b = p[1], c = p[2];
+    j[0] = a.x; j[1] = a.y; j[2] = b.x; j[3] = b.y; j[4] = c.x; j[5] = c.y;
+  }
+}
+
+// Geometry of site number ic of colour c: its neighbours' indices in the
+// other colour of the colour-split layout (its own index is ic), its natural
+// index x + L (y + L z), and, for bonds read from global memory, the
+// parity-split storage indices of the site and of its -x, -y, -z neighbours.
+struct ResidentSite {
+  int jxp, jxm, jyp, jym, jzp, jzm;  // neighbours, colour-split index
+  int i_nat;
+  int gi, gxm, gym, gzm;             // global storage index (site, -x, -y, -z)
+};
+
+template <bool GLOBAL_J>
+__device__ __forceinline__ ResidentSite resident_site(int ic, int colour, int L) {
   const int half = L >> 1;
-  const int LL = L * L;
-  const int n_col = N >> 1;
-  const size_t plane = static_cast<size_t>(N) * V;
-  for (int w = threadIdx.x; w < G_set * n_col; w += blockDim.x) {
-    const int g = w / n_col;
-    const int ic = w - g * n_col;
-    const int row = ic / half;
-    const int k = ic - row * half;
-    const int y = row % L;
-    const int z = row / L;
-    const int x = 2 * k + ((colour + y + z) & 1);
-    const int i_nat = x + L * row;
-    const int i = site_of<true>(x, row, L);
-    const int ixm = site_of<true>((x == 0) ? L - 1 : x - 1, row, L);
-    const int ixp = site_of<true>((x == L - 1) ? 0 : x + 1, row, L);
-    const int iym = (y == 0) ? i + (L - 1) * L : i - L;
-    const int iyp = (y == L - 1) ? i - (L - 1) * L : i + L;
-    const int izm = (z == 0) ? i + (L - 1) * LL : i - LL;
-    const int izp = (z == L - 1) ? i - (L - 1) * LL : i + LL;
-    float* base = sp + static_cast<size_t>(g) * 3 * plane;
-    float h[3][V], hf[3][V], hb[3][V], j[6], s[3][V];
-    zero3<V>(hf);
-    zero3<V>(hb);
-    load_bond<PREC>(Jb, i, j);                          lds_plane<V>(base, plane, ixp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jb, N + i, j);                      lds_plane<V>(base, plane, iyp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + i, j);   lds_plane<V>(base, plane, izp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jb, ixm, j);                        lds_plane<V>(base, plane, ixm, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(Jb, N + iym, j);                    lds_plane<V>(base, plane, iym, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + izm, j); lds_plane<V>(base, plane, izm, s); add_bond<V>(j, s, hb);
-    combine_field<V>(hf, hb, h);
+  const int row = ic / half;
+  const int k = ic - row * half;
+  const int y = row % L;
+  const int z = row / L;
+  const int p = (colour + y + z) & 1;                  // x parity of the site
+  const int x = 2 * k + p;
+  ResidentSite r;
+  const int rb = row * half;
+  r.jxp = rb + (p ? ((k + 1 == half) ? 0 : k + 1) : k);
+  r.jxm = rb + (p ? k : ((k == 0) ? half - 1 : k - 1));
+  const int hy = half, hz = half * L;
+  r.jyp = (y == L - 1) ? ic - (L - 1) * hy : ic + hy;
+  r.jym = (y == 0) ? ic + (L - 1) * hy : ic - hy;
+  r.jzp = (z == L - 1) ? ic - (L - 1) * hz : ic + hz;
+  r.jzm = (z == 0) ? ic + (L - 1) * hz : ic - hz;
+  r.i_nat = x + L * row;
+  if constexpr (GLOBAL_J) {
+    const int LL = L * L;
+    r.gi = site_of<true>(x, row, L);
+    r.gxm = site_of<true>((x == 0) ? L - 1 : x - 1, row, L);
+    r.gym = (y == 0) ? r.gi + (L - 1) * L : r.gi - L;
+    r.gzm = (z == 0) ? r.gi + (L - 1) * LL : r.gi - LL;
+  }
+  return r;
+}
+
+// Local field (Eq. 3) at site ic of colour c of one resident lattice group:
+// forward bonds (+x, +y, +z, stored at the site) into hf, backward bonds
+// (-x, -y, -z, stored at the neighbour) into hb, in the streaming kernels'
+// order.  sg: the group's spins, colour-split.  Js / Jg: resident or global
+// bonds.
+template <int V, int PREC, bool JS>
+__device__ __forceinline__ void resident_field(const float* sg, const void* Js, const void* Jg, int N,
+                                               int colour, int ic, const ResidentSite& r,
+                                               float (&h)[3][V]) {
+  const int hN = N >> 1;
+  const int plane = N * V;
+  const float* so = sg + (colour ^ 1) * hN * V;          // neighbours' colour
+  const int c_own = colour * hN, c_nb = (colour ^ 1) * hN;
+  float hf[3][V], hb[3][V], j[6], s[3][V];
+  zero3<V>(hf);
+  zero3<V>(hb);
+  if constexpr (JS) {
+    lds_bond<PREC>(Js, c_own + ic, j);           lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
+    lds_bond<PREC>(Js, N + c_own + ic, j);       lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
+    lds_bond<PREC>(Js, 2 * N + c_own + ic, j);   lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
+    lds_bond<PREC>(Js, c_nb + r.jxm, j);         lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
+    lds_bond<PREC>(Js, N + c_nb + r.jym, j);     lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
+    lds_bond<PREC>(Js, 2 * N + c_nb + r.jzm, j); lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
+  } else {
+    const size_t n = static_cast<size_t>(N);
+    load_bond<PREC>(Jg, r.gi, j);                lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, n + r.gi, j);            lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, 2 * n + r.gi, j);        lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, r.gxm, j);               lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(Jg, n + r.gym, j);           lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(Jg, 2 * n + r.gzm, j);       lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
+  }
+  combine_field<V>(hf, hb, h);
+}
+
+// One colour half-sweep (KIND: heat-bath or overrelaxation) of the resident
+// replica set.  The (site, group) pairs of the colour are spread over the
+// threads, consecutive threads on consecutive sites of one group.
+template <int KIND, int V, int PREC, bool JS>
+__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, int L, int N,
+                                                    int G_set, int colour, const float* beta_lat,
+                                                    uint32_t lat_base, uint32_t t, uint2 key) {
+  const int hN = N >> 1;
+  const int plane = N * V;
+  for (int w = threadIdx.x; w < G_set * hN; w += blockDim.x) {
+    const int g = w / hN;
+    const int ic = w - g * hN;
+    const ResidentSite r = resident_site<!JS>(ic, colour, L);
+    float* sg = sp + g * 3 * plane;
+    float h[3][V];
+    resident_field<V, PREC, JS>(sg, Js, Jg, N, colour, ic, r, h);
+    float* own = sg + colour * hN * V;
     float o[3][V];
     if constexpr (KIND == kHB) {
       const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
-      const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(i_nat), lat0 >> 1, t, kTagHeatBath), key);
+      const uint4 u = philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const uint32_t lat = lat0 + v;
-        heat_bath_draw(h[0][v], h[1][v], h[2][v], beta_lat[g * V + v], (lat & 1u) ? r.z : r.x,
-                       (lat & 1u) ? r.w : r.y, o[0][v], o[1][v], o[2][v]);
+        heat_bath_draw(h[0][v], h[1][v], h[2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
+                       (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
       }
-      sts_plane<V>(base, plane, i, o);
     } else {
-      lds_plane<V>(base, plane, i, o);
+      lds_plane<V>(own, plane, ic, o);
       overrelax_v<V>(h, o);
-      sts_plane<V>(base, plane, i, o);
     }
+    sts_plane<V>(own, plane, ic, o);
   }
 }
 
 // Energies of the resident lattices, E = -sum over white sites of s.h
 // (every bond has one white end): per group, per-thread FP32 terms summed in
 // FP64, warp sums, then a fixed-order sum over warps.
-template <int V, int PREC>
-__device__ __forceinline__ void resident_energies(const float* sp, const void* Jb, int L, int N, int G_set,
-                                                  double* s_E, double (*s_red)[V]) {
-  const int half = L >> 1;
-  const int LL = L * L;
-  const size_t plane = static_cast<size_t>(N) * V;
+template <int V, int PREC, bool JS>
+__device__ __forceinline__ void resident_energies(const float* sp, const void* Js, const void* Jg, int L, int N,
+                                                  int G_set, double* s_E, double (*s_red)[V]) {
+  const int hN = N >> 1;
+  const int plane = N * V;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int g = 0; g < G_set; ++g) {
-    const float* base = sp + static_cast<size_t>(g) * 3 * plane;
+    const float* sg = sp + g * 3 * plane;
     double acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.0;
-    for (int ic = threadIdx.x; ic < (N >> 1); ic += blockDim.x) {
-      const int row = ic / half;
-      const int k = ic - row * half;
-      const int y = row % L;
-      const int z = row / L;
-      const int x = 2 * k + ((1 + y + z) & 1);
-      const int i = site_of<true>(x, row, L);
-      const int ixm = site_of<true>((x == 0) ? L - 1 : x - 1, row, L);
-      const int ixp = site_of<true>((x == L - 1) ? 0 : x + 1, row, L);
-      const int iym = (y == 0) ? i + (L - 1) * L : i - L;
-      const int iyp = (y == L - 1) ? i - (L - 1) * L : i + L;
-      const int izm = (z == 0) ? i + (L - 1) * LL : i - LL;
-      const int izp = (z == L - 1) ? i - (L - 1) * LL : i + LL;
-      float h[3][V], hf[3][V], hb[3][V], j[6], s[3][V], o[3][V];
-      zero3<V>(hf);
-      zero3<V>(hb);
-      load_bond<PREC>(Jb, i, j);                          lds_plane<V>(base, plane, ixp, s); add_bond<V>(j, s, hf);
-      load_bond<PREC>(Jb, N + i, j);                      lds_plane<V>(base, plane, iyp, s); add_bond<V>(j, s, hf);
-      load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + i, j);   lds_plane<V>(base, plane, izp, s); add_bond<V>(j, s, hf);
-      load_bond<PREC>(Jb, ixm, j);                        lds_plane<V>(base, plane, ixm, s); add_bond<V>(j, s, hb);
-      load_bond<PREC>(Jb, N + iym, j);                    lds_plane<V>(base, plane, iym, s); add_bond<V>(j, s, hb);
-      load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + izm, j); lds_plane<V>(base, plane, izm, s); add_bond<V>(j, s, hb);
-      combine_field<V>(hf, hb, h);
-      lds_plane<V>(base, plane, i, o);
+    for (int ic = threadIdx.x; ic < hN; ic += blockDim.x) {
+      const ResidentSite r = resident_site<!JS>(ic, 1, L);
+      float h[3][V], o[3][V];
+      resident_field<V, PREC, JS>(sg, Js, Jg, N, 1, ic, r, h);
+      lds_plane<V>(sg + hN * V, plane, ic, o);
 #pragma unroll
       for (int v = 0; v < V; ++v)
         acc[v] -= static_cast<double>(fmaf(o[0][v], h[0][v], fmaf(o[1][v], h[1][v], o[2][v] * h[2][v])));
@@ -192,7 +247,20 @@ __device__ __forceinline__ void resident_energies(const float* sp, const void* J
   }
 }
 
-template <int V, int PREC>
+// Position in the colour-split layout of global storage index i (row-wise
+// parity split): colour * N/2 + row * L/2 + (x >> 1).
+__device__ __forceinline__ int colour_split_index(int i, int L, int N) {
+  const int half = L >> 1;
+  const int row = i / L;
+  const int rem = i - row * L;
+  const int px = rem >= half ? 1 : 0;                  // x parity block
+  const int k = rem - px * half;
+  const int y = row % L, z = row / L;
+  const int c = (px + y + z) & 1;
+  return c * (N >> 1) + row * half + k;
+}
+
+template <int V, int PREC, bool JS>
 __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentParams p) {
   extern __shared__ __align__(16) float sp[];
   __shared__ double s_E[kMaxTempsResident];
@@ -201,28 +269,48 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
   __shared__ int s_acc[kMaxTempsResident];
   __shared__ double s_red[kPersistentThreads / 32][V];
 
-  int bi = 0;
-  while (bi + 1 < p.n_buckets && static_cast<int>(blockIdx.x) >= p.b[bi + 1].cta_begin) ++bi;
-  const PersistentBucket& B = p.b[bi];
-  const int local = blockIdx.x - B.cta_begin;
-  const int sb = local / p.n_rep, r = local - sb * p.n_rep;
-  const int sg = B.sample_ids[sb];
-  const int NT = p.NT, L = B.L, N = B.N;
+  const int sb = blockIdx.x / p.n_rep, r = blockIdx.x - sb * p.n_rep;
+  const int sg = p.sample_ids[sb];
+  const int NT = p.NT, L = p.L, N = p.N;
   const int G_set = NT / V;                               // groups of this replica set
-  const size_t set_floats = static_cast<size_t>(NT) * 3 * N;
-  float* gsp = B.spins + (static_cast<size_t>(sb) * B.G + static_cast<size_t>(r) * G_set) * 3 * N * V;
-  const void* Jb = (PREC == kPrecF16)
-                       ? static_cast<const void*>(static_cast<const uint4*>(B.J) + static_cast<size_t>(sb) * 3 * N)
-                       : static_cast<const void*>(static_cast<const float*>(B.J) + static_cast<size_t>(sb) * 3 * N * 6);
+  float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * G_set) * 3 * N * V;
+  const void* Jg = (PREC == kPrecF16)
+                       ? static_cast<const void*>(static_cast<const uint4*>(p.J) + static_cast<size_t>(sb) * 3 * N)
+                       : static_cast<const void*>(static_cast<const float*>(p.J) + static_cast<size_t>(sb) * 3 * N * 6);
+  void* Js = sp + static_cast<size_t>(NT) * 3 * N;        // after the spins (16-byte aligned)
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(r * NT);
   const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
 
-  // replica set -> shared memory (contiguous, 16-byte aligned)
+  // replica set -> shared memory, parity-split rows -> colour split; one
+  // element = the V interleaved lattices of a site
+  using VecT = typename std::conditional<V == 2, float2, float>::type;
   {
-    const float4* src = reinterpret_cast<const float4*>(gsp);
-    float4* dst = reinterpret_cast<float4*>(sp);
-    for (size_t q = threadIdx.x; q < set_floats / 4; q += blockDim.x) dst[q] = src[q];
+    const VecT* src = reinterpret_cast<const VecT*>(gsp);
+    VecT* dst = reinterpret_cast<VecT*>(sp);
+    for (int q = threadIdx.x; q < G_set * 3 * N; q += blockDim.x) {
+      const int gc = q / N, i = q - gc * N;
+      dst[gc * N + colour_split_index(i, L, N)] = src[q];
+    }
+  }
+  if constexpr (JS) {
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+      const int d = q / N, i = q - d * N;
+      const int o = d * N + colour_split_index(i, L, N);
+      if constexpr (PREC == kPrecF16) {
+        const uint4 u = static_cast<const uint4*>(Jg)[q];
+        uint32_t* w = static_cast<uint32_t*>(Js) + 3 * o;
+        w[0] = u.x;
+        w[1] = u.y;
+        w[2] = u.z;
+      } else {
+        const float2* s2 = reinterpret_cast<const float2*>(static_cast<const float*>(Jg) + 6 * static_cast<size_t>(q));
+        float2* d2 = reinterpret_cast<float2*>(static_cast<float*>(Js) + 6 * o);
+        d2[0] = s2[0];
+        d2[1] = s2[1];
+        d2[2] = s2[2];
+      }
+    }
   }
   if (threadIdx.x < NT) {
     const int k = threadIdx.x;
@@ -236,16 +324,16 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
   for (int step = 0; step < p.steps; ++step) {
     const uint32_t t = t_hb0 + static_cast<uint32_t>(step);
     for (int c = 0; c < 2; ++c) {
-      resident_half_sweep<kHB, V, PREC>(sp, Jb, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
+      resident_half_sweep<kHB, V, PREC, JS>(sp, Js, Jg, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
       __syncthreads();
     }
     for (int o = 0; o < p.n_or; ++o) {
       for (int c = 0; c < 2; ++c) {
-        resident_half_sweep<kOR, V, PREC>(sp, Jb, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
+        resident_half_sweep<kOR, V, PREC, JS>(sp, Js, Jg, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
         __syncthreads();
       }
     }
-    resident_energies<V, PREC>(sp, Jb, L, N, G_set, s_E, s_red);
+    resident_energies<V, PREC, JS>(sp, Js, Jg, L, N, G_set, s_E, s_red);
     // parallel tempering within the replica set (App. A.1)
     if (threadIdx.x == 0 && NT > 1) {
       const uint32_t tp = t_pt0 + static_cast<uint32_t>(step);
@@ -267,9 +355,12 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
 
   // shared memory -> replica set; energies, labels and acceptances out
   {
-    const float4* src = reinterpret_cast<const float4*>(sp);
-    float4* dst = reinterpret_cast<float4*>(gsp);
-    for (size_t q = threadIdx.x; q < set_floats / 4; q += blockDim.x) dst[q] = src[q];
+    const VecT* src = reinterpret_cast<const VecT*>(sp);
+    VecT* dst = reinterpret_cast<VecT*>(gsp);
+    for (int q = threadIdx.x; q < G_set * 3 * N; q += blockDim.x) {
+      const int gc = q / N, i = q - gc * N;
+      dst[q] = src[gc * N + colour_split_index(i, L, N)];
+    }
   }
   if (threadIdx.x < NT) {
     const int k = threadIdx.x;

@@ -16,6 +16,8 @@ CASES = [
     ([12, 8, 8], 4, 3, hsg.F32, hsg.PLAIN, 8, 3, 7),
     ([10], 6, 2, hsg.F32, hsg.BATCHED, 2, 0, 5),
     ([8], 1, 2, hsg.F16, hsg.PLAIN, 1, 1, 3),
+    # L=12 with FP32 bonds: the bonds stay in global memory (spins 166 KB)
+    ([12, 8], 8, 2, hsg.F32, hsg.BATCHED, 2, 2, 4),
 ]
 
 
