@@ -52,7 +52,8 @@ struct Bucket {
   int m_chunks = 0, P = 0;
   double* d_mpart = nullptr;  // [S_b][NT][P][m_chunks][kNQ]
   float* d_phase = nullptr;   // [L][2]
-  bool res_js = false;        // resident steps: bonds resident in shared memory too
+  int res_js = 0;             // resident steps: bonds in global memory (0), resident as
+                              // stored (1) or resident as FP32 (2)
   size_t res_smem = 0;        // resident steps: dynamic shared memory per CTA
 };
 
@@ -338,44 +339,69 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
   return false;
 }
 
-// Resident-step kernel for (V, precision, bonds resident).
-template <int V, int PREC, bool JS>
-void* persistent_fn() {
-  return reinterpret_cast<void*>(k_persistent<V, PREC, JS>);
+// Resident-step kernel for (V, precision, bond residency, L): L = 8 and 12
+// have compile-time specialisations when the bonds are resident.
+template <int V, int PREC, int JS>
+void* persistent_fn_L(int L) {
+  if constexpr (JS == 0) {
+    return reinterpret_cast<void*>(k_persistent<V, PREC, 0, 0>);
+  } else {
+    if (L == 8) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 8>);
+    if (L == 12) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 12>);
+    return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 0>);
+  }
 }
 
-void* persistent_kernel(int V, int prec, bool js) {
-  if (V == 2) {
-    if (prec == HSG_F16) return js ? persistent_fn<2, kPrecF16, true>() : persistent_fn<2, kPrecF16, false>();
-    return js ? persistent_fn<2, kPrecF32, true>() : persistent_fn<2, kPrecF32, false>();
+template <int V, int PREC>
+void* persistent_fn_js(int js, int L) {
+  if (js == 0) return persistent_fn_L<V, PREC, 0>(L);
+  if constexpr (PREC == kPrecF32) {
+    return persistent_fn_L<V, PREC, 1>(L);  // FP32 bonds are resident as stored
+  } else {
+    return js == 1 ? persistent_fn_L<V, PREC, 1>(L) : persistent_fn_L<V, PREC, 2>(L);
   }
-  if (prec == HSG_F16) return js ? persistent_fn<1, kPrecF16, true>() : persistent_fn<1, kPrecF16, false>();
-  return js ? persistent_fn<1, kPrecF32, true>() : persistent_fn<1, kPrecF32, false>();
 }
+
+void* persistent_kernel(int V, int prec, int js, int L) {
+  if (V == 2) return prec == HSG_F16 ? persistent_fn_js<2, kPrecF16>(js, L) : persistent_fn_js<2, kPrecF32>(js, L);
+  return prec == HSG_F16 ? persistent_fn_js<1, kPrecF16>(js, L) : persistent_fn_js<1, kPrecF32>(js, L);
+}
+
+constexpr int kResidentThreads = 512;
 
 // Plans the resident steps of every bucket: spins 12 N_T N bytes, plus the
-// bonds (3 N per sample) when both fit in the block's shared memory; sets the
-// kernels' dynamic shared-memory limits.
+// bonds (3 N per sample) when they fit beside them -- converted to FP32
+// (JS = 2) unless that lowers the CTAs per SM, else as stored (JS = 1) -- or
+// read from global memory (JS = 0).
 hsg_status plan_persistent(hsg_ctx* h) {
   int dev = 0, optin = 0;
   HSG_CUDA(cudaGetDevice(&dev));
   HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  size_t need[2] = {0, 0};
   for (Bucket& b : h->buckets) {
-    cudaFuncAttributes fa;
-    HSG_CUDA(cudaFuncGetAttributes(&fa, persistent_kernel(h->V, h->prec, true)));
-    const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
     const size_t spins = static_cast<size_t>(12) * h->NT * b.N;
-    const size_t bonds = static_cast<size_t>(3) * b.N * (h->prec == HSG_F16 ? 12 : 24);
-    if (spins > budget) return fail(HSG_EINVAL, "a replica set does not fit in shared memory");
-    b.res_js = spins + bonds <= budget;
-    b.res_smem = b.res_js ? spins + bonds : spins;
-    need[b.res_js] = std::max(need[b.res_js], b.res_smem);
+    const size_t bond_bytes[3] = {0, static_cast<size_t>(h->prec == HSG_F16 ? 12 : 24), 24};
+    int best_js = -1, best_occ = 0;
+    size_t best_smem = 0;
+    for (int js = (h->prec == HSG_F16 ? 2 : 1); js >= 0; --js) {
+      void* fn = persistent_kernel(h->V, h->prec, js, b.L);
+      cudaFuncAttributes fa;
+      HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
+      const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+      const size_t smem = spins + 3 * static_cast<size_t>(b.N) * bond_bytes[js];
+      if (smem > budget) continue;
+      HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(budget)));
+      int occ = 0;
+      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kResidentThreads, smem));
+      if (occ > best_occ) {
+        best_js = js;
+        best_occ = occ;
+        best_smem = smem;
+      }
+    }
+    if (best_js < 0) return fail(HSG_EINVAL, "a replica set does not fit in shared memory");
+    b.res_js = best_js;
+    b.res_smem = best_smem;
   }
-  for (int js = 0; js < 2; ++js)
-    if (need[js] > 0)
-      HSG_CUDA(cudaFuncSetAttribute(persistent_kernel(h->V, h->prec, js != 0),
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(need[js])));
   return HSG_OK;
 }
 
@@ -406,8 +432,8 @@ hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
     p.counters = h->d_counters;
     void* args[] = {&p};
     *h->launch_sink += 1;
-    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js), dim3(b.S_b * h->n_rep),
-                              dim3(kPersistentThreads), args, b.res_smem, st));
+    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L), dim3(b.S_b * h->n_rep),
+                              dim3(kResidentThreads), args, b.res_smem, st));
   }
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }

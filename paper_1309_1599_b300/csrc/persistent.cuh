@@ -15,9 +15,19 @@
 // the sites a warp updates and each of their six neighbours are consecutive
 // words and the accesses are free of bank conflicts:
 //   spins  [G_set][3][2 colours][N/2][V] floats
-//   bonds  [3 directions][2 colours][N/2] x 6 entries (FP16: 12 B, FP32: 24 B),
-//          the bond (x, x+mu) stored at its lower site x, when they fit
-//          beside the spins (JS); otherwise read from global memory.
+//   bonds  [3 directions][2 colours][N/2] x 6 entries, the bond (x, x+mu)
+//          stored at its lower site x, when they fit beside the spins:
+//          JS = 1 in the stored precision (FP16: 12 B, FP32: 24 B), JS = 2
+//          converted to FP32 once at the start (24 B); JS = 0: read from
+//          global memory.
+//
+// Work split.  The warps are divided among the lattice groups of the set
+// (wpg warps per group, or one warp looping over several groups when there
+// are more groups than warps), so each thread updates sites of one group at
+// a time; the energies (E = -sum over white sites of s.h, every bond having
+// one white end) are accumulated in the last white half-sweep of the step,
+// where the white sites' fields are computed anyway, and reduced per group
+// in a fixed order.
 //
 // The arithmetic is that of the streaming kernels: the same field summation
 // (forward and backward partial sums), the same single-spin updates and the
@@ -32,7 +42,7 @@
 
 namespace hsg {
 
-constexpr int kPersistentThreads = 512;
+constexpr int kPersistentMaxThreads = 1024;
 constexpr int kMaxTempsResident = 64;
 constexpr int kMaxStepsPerLaunch = 256;
 
@@ -51,9 +61,6 @@ struct PersistentParams {
   const uint32_t* counters;  // [0] heat-bath sweeps, [1] PT sweeps (at launch)
 };
 
-// bytes of one bond (6 entries) in the resident layout
-template <int PREC>
-constexpr int resident_bond_bytes() { return PREC == kPrecF16 ? 12 : 24; }
 
 template <int V>
 __device__ __forceinline__ void lds_plane(const float* base, int plane, int i, float (&s)[3][V]) {
@@ -111,7 +118,7 @@ struct ResidentSite {
 };
 
 template <bool GLOBAL_J>
-__device__ __forceinline__ ResidentSite resident_site(int ic, int colour, int L) {
+__device__ __forceinline__ ResidentSite resident_site(int ic, int colour, const int L) {
   const int half = L >> 1;
   const int row = ic / half;
   const int k = ic - row * half;
@@ -144,10 +151,11 @@ __device__ __forceinline__ ResidentSite resident_site(int ic, int colour, int L)
 // (-x, -y, -z, stored at the neighbour) into hb, in the streaming kernels'
 // order.  sg: the group's spins, colour-split.  Js / Jg: resident or global
 // bonds.
-template <int V, int PREC, bool JS>
-__device__ __forceinline__ void resident_field(const float* sg, const void* Js, const void* Jg, int N,
+template <int V, int PREC, int JS>
+__device__ __forceinline__ void resident_field(const float* sg, const void* Js, const void* Jg, const int N,
                                                int colour, int ic, const ResidentSite& r,
                                                float (&h)[3][V]) {
+  constexpr int BP = JS == 2 ? kPrecF32 : PREC;        // precision of the resident bonds
   const int hN = N >> 1;
   const int plane = N * V;
   const float* so = sg + (colour ^ 1) * hN * V;          // neighbours' colour
@@ -155,13 +163,13 @@ __device__ __forceinline__ void resident_field(const float* sg, const void* Js, 
   float hf[3][V], hb[3][V], j[6], s[3][V];
   zero3<V>(hf);
   zero3<V>(hb);
-  if constexpr (JS) {
-    lds_bond<PREC>(Js, c_own + ic, j);           lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
-    lds_bond<PREC>(Js, N + c_own + ic, j);       lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
-    lds_bond<PREC>(Js, 2 * N + c_own + ic, j);   lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
-    lds_bond<PREC>(Js, c_nb + r.jxm, j);         lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
-    lds_bond<PREC>(Js, N + c_nb + r.jym, j);     lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
-    lds_bond<PREC>(Js, 2 * N + c_nb + r.jzm, j); lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
+  if constexpr (JS != 0) {
+    lds_bond<BP>(Js, c_own + ic, j);           lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, N + c_own + ic, j);       lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, 2 * N + c_own + ic, j);   lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, c_nb + r.jxm, j);         lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
+    lds_bond<BP>(Js, N + c_nb + r.jym, j);     lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
+    lds_bond<BP>(Js, 2 * N + c_nb + r.jzm, j); lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
   } else {
     const size_t n = static_cast<size_t>(N);
     load_bond<PREC>(Jg, r.gi, j);                lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
@@ -174,76 +182,78 @@ __device__ __forceinline__ void resident_field(const float* sg, const void* Js, 
   combine_field<V>(hf, hb, h);
 }
 
-// One colour half-sweep (KIND: heat-bath or overrelaxation) of the resident
-// replica set.  The (site, group) pairs of the colour are spread over the
-// threads, consecutive threads on consecutive sites of one group.
-template <int KIND, int V, int PREC, bool JS>
-__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, int L, int N,
-                                                    int G_set, int colour, const float* beta_lat,
-                                                    uint32_t lat_base, uint32_t t, uint2 key) {
-  const int hN = N >> 1;
-  const int plane = N * V;
-  for (int w = threadIdx.x; w < G_set * hN; w += blockDim.x) {
-    const int g = w / hN;
-    const int ic = w - g * hN;
-    const ResidentSite r = resident_site<!JS>(ic, colour, L);
-    float* sg = sp + g * 3 * plane;
-    float h[3][V];
-    resident_field<V, PREC, JS>(sg, Js, Jg, N, colour, ic, r, h);
-    float* own = sg + colour * hN * V;
-    float o[3][V];
-    if constexpr (KIND == kHB) {
-      const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
-      const uint4 u = philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const uint32_t lat = lat0 + v;
-        heat_bath_draw(h[0][v], h[1][v], h[2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
-                       (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
-      }
-    } else {
-      lds_plane<V>(own, plane, ic, o);
-      overrelax_v<V>(h, o);
-    }
-    sts_plane<V>(own, plane, ic, o);
-  }
+// Warp layout of a CTA over the G_set lattice groups of its replica set.
+struct ResidentWarps {
+  int wpg;    // warps per group
+  int gpp;    // groups in flight at once
+  int g0;     // this warp's first group (>= gpp: idle in the sweeps)
+  int sub;    // this warp's index within its group
+};
+
+__device__ __forceinline__ ResidentWarps resident_warps(int G_set) {
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  ResidentWarps rw;
+  rw.wpg = W >= G_set ? W / G_set : 1;
+  rw.gpp = W / rw.wpg;
+  rw.g0 = warp / rw.wpg;
+  rw.sub = warp - rw.g0 * rw.wpg;
+  return rw;
 }
 
-// Energies of the resident lattices, E = -sum over white sites of s.h
-// (every bond has one white end): per group, per-thread FP32 terms summed in
-// FP64, warp sums, then a fixed-order sum over warps.
-template <int V, int PREC, bool JS>
-__device__ __forceinline__ void resident_energies(const float* sp, const void* Js, const void* Jg, int L, int N,
-                                                  int G_set, double* s_E, double (*s_red)[V]) {
+// One colour half-sweep (KIND: heat-bath or overrelaxation) of the resident
+// replica set.  With ENERGY (the last white half-sweep of a step), each warp
+// also sums -s.h over its sites of each group it updates (FP32 terms in
+// FP64) into s_part[(g * wpg + sub) * V + v].
+template <int KIND, bool ENERGY, int V, int PREC, int JS, int LT>
+__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, const int Lrt,
+                                                    const ResidentWarps& rw, int G_set, int colour,
+                                                    const float* beta_lat, uint32_t lat_base, uint32_t t,
+                                                    uint2 key, double* s_part) {
+  const int L = LT > 0 ? LT : Lrt;
+  const int N = L * L * L;
   const int hN = N >> 1;
   const int plane = N * V;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int g = 0; g < G_set; ++g) {
-    const float* sg = sp + g * 3 * plane;
+  const int lane = threadIdx.x & 31;
+  if (rw.g0 >= rw.gpp) return;
+  for (int g = rw.g0; g < G_set; g += rw.gpp) {
+    float* sg = sp + g * 3 * plane;
+    float* own = sg + colour * hN * V;
     double acc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.0;
-    for (int ic = threadIdx.x; ic < hN; ic += blockDim.x) {
-      const ResidentSite r = resident_site<!JS>(ic, 1, L);
-      float h[3][V], o[3][V];
-      resident_field<V, PREC, JS>(sg, Js, Jg, N, 1, ic, r, h);
-      lds_plane<V>(sg + hN * V, plane, ic, o);
+    for (int ic = rw.sub * 32 + lane; ic < hN; ic += rw.wpg * 32) {
+      const ResidentSite r = resident_site<JS == 0>(ic, colour, L);
+      float h[3][V];
+      resident_field<V, PREC, JS>(sg, Js, Jg, N, colour, ic, r, h);
+      float o[3][V];
+      if constexpr (KIND == kHB) {
+        const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
+        const uint4 u =
+            philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
 #pragma unroll
-      for (int v = 0; v < V; ++v)
-        acc[v] -= static_cast<double>(fmaf(o[0][v], h[0][v], fmaf(o[1][v], h[1][v], o[2][v] * h[2][v])));
-    }
+        for (int v = 0; v < V; ++v) {
+          const uint32_t lat = lat0 + v;
+          heat_bath_draw(h[0][v], h[1][v], h[2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
+                         (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
+        }
+      } else {
+        lds_plane<V>(own, plane, ic, o);
+        overrelax_v<V>(h, o);
+      }
+      sts_plane<V>(own, plane, ic, o);
+      if constexpr (ENERGY) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const double d = warp_sum(acc[v]);
-      if (lane == 0) s_red[warp][v] = d;
+        for (int v = 0; v < V; ++v)
+          acc[v] -= static_cast<double>(fmaf(o[0][v], h[0][v], fmaf(o[1][v], h[1][v], o[2][v] * h[2][v])));
+      }
     }
-    __syncthreads();
-    if (threadIdx.x < V) {
-      double e = 0.0;
-      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) e += s_red[w][threadIdx.x];
-      s_E[g * V + threadIdx.x] = e;
+    if constexpr (ENERGY) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const double d = warp_sum(acc[v]);
+        if (lane == 0) s_part[(g * rw.wpg + rw.sub) * V + v] = d;
+      }
     }
-    __syncthreads();
   }
 }
 
@@ -260,18 +270,23 @@ __device__ __forceinline__ int colour_split_index(int i, int L, int N) {
   return c * (N >> 1) + row * half + k;
 }
 
-template <int V, int PREC, bool JS>
-__global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentParams p) {
+// K whole steps of every replica set of one L.  V: lattices per element;
+// PREC: stored coupling precision; JS: bond residency (see above); LT: L as
+// a compile-time constant, or 0 for the runtime p.L.
+template <int V, int PREC, int JS, int LT>
+__global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(PersistentParams p) {
   extern __shared__ __align__(16) float sp[];
   __shared__ double s_E[kMaxTempsResident];
+  __shared__ double s_part[kMaxTempsResident * 2];  // per (group, warp of the group, lattice)
   __shared__ float s_beta_lat[kMaxTempsResident];   // beta of each local lattice
   __shared__ int s_perm[kMaxTempsResident];         // temperature -> local lattice
   __shared__ int s_acc[kMaxTempsResident];
-  __shared__ double s_red[kPersistentThreads / 32][V];
 
   const int sb = blockIdx.x / p.n_rep, r = blockIdx.x - sb * p.n_rep;
   const int sg = p.sample_ids[sb];
-  const int NT = p.NT, L = p.L, N = p.N;
+  const int NT = p.NT;
+  const int L = LT > 0 ? LT : p.L;
+  const int N = L * L * L;
   const int G_set = NT / V;                               // groups of this replica set
   float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * G_set) * 3 * N * V;
   const void* Jg = (PREC == kPrecF16)
@@ -281,6 +296,7 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(r * NT);
   const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
+  const ResidentWarps rw = resident_warps(G_set);
 
   // replica set -> shared memory, parity-split rows -> colour split; one
   // element = the V interleaved lattices of a site
@@ -293,11 +309,18 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
       dst[gc * N + colour_split_index(i, L, N)] = src[q];
     }
   }
-  if constexpr (JS) {
+  if constexpr (JS != 0) {
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
       const int d = q / N, i = q - d * N;
       const int o = d * N + colour_split_index(i, L, N);
-      if constexpr (PREC == kPrecF16) {
+      if constexpr (JS == 2) {
+        float j[6];
+        load_bond<PREC>(Jg, q, j);
+        float2* d2 = reinterpret_cast<float2*>(static_cast<float*>(Js) + 6 * o);
+        d2[0] = make_float2(j[0], j[1]);
+        d2[1] = make_float2(j[2], j[3]);
+        d2[2] = make_float2(j[4], j[5]);
+      } else if constexpr (PREC == kPrecF16) {
         const uint4 u = static_cast<const uint4*>(Jg)[q];
         uint32_t* w = static_cast<uint32_t*>(Js) + 3 * o;
         w[0] = u.x;
@@ -323,17 +346,39 @@ __global__ void __launch_bounds__(kPersistentThreads) k_persistent(PersistentPar
 
   for (int step = 0; step < p.steps; ++step) {
     const uint32_t t = t_hb0 + static_cast<uint32_t>(step);
-    for (int c = 0; c < 2; ++c) {
-      resident_half_sweep<kHB, V, PREC, JS>(sp, Js, Jg, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
+    resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 0, s_beta_lat, lat_base, t,
+                                                     p.key, s_part);
+    __syncthreads();
+    if (p.n_or == 0) {
+      resident_half_sweep<kHB, true, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+                                                      p.key, s_part);
+    } else {
+      resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+                                                       p.key, s_part);
       __syncthreads();
-    }
-    for (int o = 0; o < p.n_or; ++o) {
-      for (int c = 0; c < 2; ++c) {
-        resident_half_sweep<kOR, V, PREC, JS>(sp, Js, Jg, L, N, G_set, c, s_beta_lat, lat_base, t, p.key);
+      for (int o = 0; o < p.n_or; ++o) {
+        resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 0, s_beta_lat, lat_base,
+                                                         t, p.key, s_part);
         __syncthreads();
+        if (o + 1 < p.n_or) {
+          resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base,
+                                                           t, p.key, s_part);
+          __syncthreads();
+        } else {
+          resident_half_sweep<kOR, true, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base,
+                                                          t, p.key, s_part);
+        }
       }
     }
-    resident_energies<V, PREC, JS>(sp, Js, Jg, L, N, G_set, s_E, s_red);
+    __syncthreads();
+    // energies of the local lattices, fixed-order sums of the warp partials
+    if (threadIdx.x < NT) {
+      const int g = threadIdx.x / V, v = threadIdx.x - g * V;
+      double e = 0.0;
+      for (int w = 0; w < rw.wpg; ++w) e += s_part[(g * rw.wpg + w) * V + v];
+      s_E[threadIdx.x] = e;
+    }
+    __syncthreads();
     // parallel tempering within the replica set (App. A.1)
     if (threadIdx.x == 0 && NT > 1) {
       const uint32_t tp = t_pt0 + static_cast<uint32_t>(step);

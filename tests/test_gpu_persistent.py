@@ -18,6 +18,8 @@ CASES = [
     ([8], 1, 2, hsg.F16, hsg.PLAIN, 1, 1, 3),
     # L=12 with FP32 bonds: the bonds stay in global memory (spins 166 KB)
     ([12, 8], 8, 2, hsg.F32, hsg.BATCHED, 2, 2, 4),
+    # heat-bath only: the energies come from the white heat-bath half-sweep
+    ([8, 12], 4, 2, hsg.F16, hsg.BATCHED, 0, 2, 4),
 ]
 
 
