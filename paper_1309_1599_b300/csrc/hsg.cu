@@ -50,6 +50,7 @@ struct Bucket {
   size_t fused_smem = 0;      // dynamic shared memory of the fused sweep
   double* d_epart = nullptr;  // [S_b*R][max(sweep_chunks, n_bands)]
   int m_chunks = 0, P = 0;
+  bool m_warp = false;        // measurement: one warp per unit (small lattices)
   double* d_mpart = nullptr;  // [S_b][NT][P][m_chunks][kNQ]
   float* d_phase = nullptr;   // [L][2]
   int res_js = 0;             // resident steps: bonds in global memory (0), resident as
@@ -521,7 +522,17 @@ hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
     const unsigned grid = static_cast<unsigned>(b.S_b * h->NT * b.P * b.m_chunks);
     const size_t smem = 2 * sizeof(float) * b.L;
     *h->launch_sink += 2;
-    if (h->V == 2) {
+    if (b.m_warp) {
+      const int n_units = b.S_b * h->NT * b.P;
+      const unsigned wgrid = static_cast<unsigned>((n_units + kMeasureThreads / 32 - 1) / (kMeasureThreads / 32));
+      if (h->V == 2) {
+        if (h->prec == HSG_F16) k_measure_warp<2, kPrecF16><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+        else k_measure_warp<2, kPrecF32><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+      } else {
+        if (h->prec == HSG_F16) k_measure_warp<1, kPrecF16><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+        else k_measure_warp<1, kPrecF32><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+      }
+    } else if (h->V == 2) {
       if (h->prec == HSG_F16) k_measure<2, kPrecF16><<<grid, kMeasureThreads, smem, st>>>(p);
       else k_measure<2, kPrecF32><<<grid, kMeasureThreads, smem, st>>>(p);
     } else {
@@ -723,7 +734,9 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     const int units = b.S_b * h->NT * b.P;
     const int by_size = std::max(1, b.N / (kMeasureThreads * 16));
     const int by_fill = std::max(1, (2 * 148 + units - 1) / units);
-    b.m_chunks = std::max(1, std::min(by_size, by_fill));
+    // small lattices (N < 4096): one warp per unit (m_chunks = 1)
+    b.m_warp = b.N < kMeasureThreads * 16;
+    b.m_chunks = b.m_warp ? 1 : std::max(1, std::min(by_size, by_fill));
     max_N = std::max<size_t>(max_N, b.N);
     const size_t n_spin = static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
     hsg_status st;

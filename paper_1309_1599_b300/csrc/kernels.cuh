@@ -452,6 +452,107 @@ __device__ __forceinline__ void add_bond1(const float (&j)[6], const float (&s)[
   h[2] = fmaf(j[4], s[0], fmaf(j[5], s[1], fmaf(j[2], s[2], h[2])));
 }
 
+// The raw sums of one site i of the replica pair (base_a, base_b), added to
+// part[kNQ].
+template <int V, int PREC>
+__device__ __forceinline__ void measure_site(const void* J, size_t jb, const float* sh_phase, const float* base_a,
+                                             const float* base_b, size_t plane, int L, int N, int i, bool do_sd,
+                                             float T, float (&part)[kNQ]) {
+  const int row = i / L, jr = i - row * L;
+  const int half = L >> 1;
+  const int x = (jr < half) ? 2 * jr : 2 * (jr - half) + 1;
+  const int y = row % L, z = row / L;
+  const int LL = L * L;
+  const int nb[6] = {site_of<true>((x == L - 1) ? 0 : x + 1, row, L),
+                     site_of<true>((x == 0) ? L - 1 : x - 1, row, L),
+                     (y == L - 1) ? i - (L - 1) * L : i + L, (y == 0) ? i + (L - 1) * L : i - L,
+                     (z == L - 1) ? i - (L - 1) * LL : i + LL, (z == 0) ? i + (L - 1) * LL : i - LL};
+  float sa[3], sbv[3];
+  load_one<V>(base_a, plane, i, sa);
+  load_one<V>(base_b, plane, i, sbv);
+  float ha[3] = {0.f, 0.f, 0.f}, hb[3] = {0.f, 0.f, 0.f};
+  float za[3], zb[3];
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    float ua[3], da[3], ub[3], db[3];
+    load_one<V>(base_a, plane, nb[2 * mu], ua);
+    load_one<V>(base_a, plane, nb[2 * mu + 1], da);
+    load_one<V>(base_b, plane, nb[2 * mu], ub);
+    load_one<V>(base_b, plane, nb[2 * mu + 1], db);
+    za[mu] = triple(ua, sa, da);
+    zb[mu] = triple(ub, sbv, db);
+    if (do_sd) {
+      float j[6];
+      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + i, j);
+      add_bond1(j, ua, ha);
+      add_bond1(j, ub, hb);
+      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + nb[2 * mu + 1], j);
+      add_bond1(j, da, ha);
+      add_bond1(j, db, hb);
+    }
+  }
+  const float q = fmaf(sa[0], sbv[0], fmaf(sa[1], sbv[1], sa[2] * sbv[2]));
+  const float c[3] = {sh_phase[2 * x], sh_phase[2 * y], sh_phase[2 * z]};
+  const float s[3] = {sh_phase[2 * x + 1], sh_phase[2 * y + 1], sh_phase[2 * z + 1]};
+  part[0] += q;
+#pragma unroll
+  for (int nu = 0; nu < 3; ++nu) {
+    part[1 + 2 * nu] = fmaf(q, c[nu], part[1 + 2 * nu]);
+    part[2 + 2 * nu] = fmaf(q, s[nu], part[2 + 2 * nu]);
+  }
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    const float kap = za[mu] * zb[mu];
+    part[7 + mu] += kap;
+#pragma unroll
+    for (int nu = 0; nu < 3; ++nu) {
+      part[10 + 2 * (3 * mu + nu)] = fmaf(kap, c[nu], part[10 + 2 * (3 * mu + nu)]);
+      part[11 + 2 * (3 * mu + nu)] = fmaf(kap, s[nu], part[11 + 2 * (3 * mu + nu)]);
+    }
+  }
+  if (do_sd) {
+    const float sha = fmaf(sa[0], ha[0], fmaf(sa[1], ha[1], sa[2] * ha[2]));
+    const float hha = fmaf(ha[0], ha[0], fmaf(ha[1], ha[1], ha[2] * ha[2]));
+    const float shb = fmaf(sbv[0], hb[0], fmaf(sbv[1], hb[1], sbv[2] * hb[2]));
+    const float hhb = fmaf(hb[0], hb[0], fmaf(hb[1], hb[1], hb[2] * hb[2]));
+    part[28] += 2.0f * T * sha - (hha - sha * sha);
+    part[29] += 2.0f * T * shb - (hhb - shb * shb);
+  }
+}
+
+// Replica pair of measurement unit `unit` = (sample, temperature k, pair pp).
+struct MeasureUnit {
+  const float* base_a;
+  const float* base_b;
+  size_t jb;
+  bool do_sd;
+  float T;
+};
+
+template <int V>
+__device__ __forceinline__ MeasureUnit measure_unit(const MeasureParams& p, int unit) {
+  const BucketView& b = p.b;
+  const int N = b.N;
+  const int pp = unit % p.P;
+  const int k = (unit / p.P) % p.NT;
+  const int sb = unit / (p.P * p.NT);
+  const int sg = b.sample_ids[sb];
+  const int slot_a = p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp) * p.NT + k];
+  const bool has_b = 2 * pp + 1 < p.n_rep;
+  const int slot_b = has_b ? p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp + 1) * p.NT + k] : slot_a;
+  const size_t plane = static_cast<size_t>(N) * V;
+  MeasureUnit m;
+  m.base_a = b.spins + (static_cast<size_t>(sb) * b.G + slot_a / V) * 3 * plane + slot_a % V;
+  m.base_b = b.spins + (static_cast<size_t>(sb) * b.G + slot_b / V) * 3 * plane + slot_b % V;
+  m.jb = static_cast<size_t>(sb) * 3 * N;
+  const double beta = p.beta[k];
+  m.do_sd = beta > 0.0;
+  m.T = m.do_sd ? static_cast<float>(1.0 / beta) : 0.0f;
+  return m;
+}
+
+// One block per (unit, chunk of sites).  FP32 within batches of 8 sites,
+// FP64 across batches and threads.
 template <int V, int PREC>
 __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
   extern __shared__ float sh_phase[];  // [L][2]
@@ -463,20 +564,8 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
 
   const int unit = blockIdx.x / p.chunks;
   const int chunk = blockIdx.x - unit * p.chunks;
-  const int pp = unit % p.P;
-  const int k = (unit / p.P) % p.NT;
-  const int sb = unit / (p.P * p.NT);
-  const int sg = b.sample_ids[sb];
-  const int slot_a = p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp) * p.NT + k];
-  const bool has_b = 2 * pp + 1 < p.n_rep;
-  const int slot_b = has_b ? p.perm[(static_cast<size_t>(sg) * p.n_rep + 2 * pp + 1) * p.NT + k] : slot_a;
+  const MeasureUnit m = measure_unit<V>(p, unit);
   const size_t plane = static_cast<size_t>(N) * V;
-  const float* base_a = b.spins + (static_cast<size_t>(sb) * b.G + slot_a / V) * 3 * plane + slot_a % V;
-  const float* base_b = b.spins + (static_cast<size_t>(sb) * b.G + slot_b / V) * 3 * plane + slot_b % V;
-  const double beta = p.beta[k];
-  const bool do_sd = beta > 0.0;
-  const float T = do_sd ? static_cast<float>(1.0 / beta) : 0.0f;
-  const size_t jb = static_cast<size_t>(sb) * 3 * N;
 
   double acc[kNQ];
 #pragma unroll
@@ -490,66 +579,7 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
   const int end = min(N, start + per_chunk);
   int batch = 0;
   for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
-    const int row = i / L, jr = i - row * L;
-    const int half = L >> 1;
-    const int x = (jr < half) ? 2 * jr : 2 * (jr - half) + 1;
-    const int y = row % L, z = row / L;
-    const int LL = L * L;
-    const int nb[6] = {site_of<true>((x == L - 1) ? 0 : x + 1, row, L),
-                       site_of<true>((x == 0) ? L - 1 : x - 1, row, L),
-                       (y == L - 1) ? i - (L - 1) * L : i + L, (y == 0) ? i + (L - 1) * L : i - L,
-                       (z == L - 1) ? i - (L - 1) * LL : i + LL, (z == 0) ? i + (L - 1) * LL : i - LL};
-    float sa[3], sbv[3];
-    load_one<V>(base_a, plane, i, sa);
-    load_one<V>(base_b, plane, i, sbv);
-    float ha[3] = {0.f, 0.f, 0.f}, hb[3] = {0.f, 0.f, 0.f};
-    float za[3], zb[3];
-#pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      float ua[3], da[3], ub[3], db[3];
-      load_one<V>(base_a, plane, nb[2 * mu], ua);
-      load_one<V>(base_a, plane, nb[2 * mu + 1], da);
-      load_one<V>(base_b, plane, nb[2 * mu], ub);
-      load_one<V>(base_b, plane, nb[2 * mu + 1], db);
-      za[mu] = triple(ua, sa, da);
-      zb[mu] = triple(ub, sbv, db);
-      if (do_sd) {
-        float j[6];
-        load_bond<PREC>(b.J, jb + static_cast<size_t>(mu) * N + i, j);
-        add_bond1(j, ua, ha);
-        add_bond1(j, ub, hb);
-        load_bond<PREC>(b.J, jb + static_cast<size_t>(mu) * N + nb[2 * mu + 1], j);
-        add_bond1(j, da, ha);
-        add_bond1(j, db, hb);
-      }
-    }
-    const float q = fmaf(sa[0], sbv[0], fmaf(sa[1], sbv[1], sa[2] * sbv[2]));
-    const float c[3] = {sh_phase[2 * x], sh_phase[2 * y], sh_phase[2 * z]};
-    const float s[3] = {sh_phase[2 * x + 1], sh_phase[2 * y + 1], sh_phase[2 * z + 1]};
-    part[0] += q;
-#pragma unroll
-    for (int nu = 0; nu < 3; ++nu) {
-      part[1 + 2 * nu] = fmaf(q, c[nu], part[1 + 2 * nu]);
-      part[2 + 2 * nu] = fmaf(q, s[nu], part[2 + 2 * nu]);
-    }
-#pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      const float kap = za[mu] * zb[mu];
-      part[7 + mu] += kap;
-#pragma unroll
-      for (int nu = 0; nu < 3; ++nu) {
-        part[10 + 2 * (3 * mu + nu)] = fmaf(kap, c[nu], part[10 + 2 * (3 * mu + nu)]);
-        part[11 + 2 * (3 * mu + nu)] = fmaf(kap, s[nu], part[11 + 2 * (3 * mu + nu)]);
-      }
-    }
-    if (do_sd) {
-      const float sha = fmaf(sa[0], ha[0], fmaf(sa[1], ha[1], sa[2] * ha[2]));
-      const float hha = fmaf(ha[0], ha[0], fmaf(ha[1], ha[1], ha[2] * ha[2]));
-      const float shb = fmaf(sbv[0], hb[0], fmaf(sbv[1], hb[1], sbv[2] * hb[2]));
-      const float hhb = fmaf(hb[0], hb[0], fmaf(hb[1], hb[1], hb[2] * hb[2]));
-      part[28] += 2.0f * T * sha - (hha - sha * sha);
-      part[29] += 2.0f * T * shb - (hhb - shb * shb);
-    }
+    measure_site<V, PREC>(b.J, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
     if (++batch == 8) {
 #pragma unroll
       for (int qq = 0; qq < kNQ; ++qq) {
@@ -574,6 +604,49 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
     for (int w = 0; w < kMeasureThreads / 32; ++w) sum += red[w][threadIdx.x];
     p.partial[(static_cast<size_t>(unit) * p.chunks + chunk) * kNQ + threadIdx.x] = sum;
   }
+}
+
+// Small lattices: one warp per unit over all its sites (p.chunks == 1), so
+// the reduction is a warp sum only.  Same per-site terms and batching as
+// k_measure.
+template <int V, int PREC>
+__global__ void __launch_bounds__(kMeasureThreads) k_measure_warp(MeasureParams p, int n_units) {
+  extern __shared__ float sh_phase[];  // [L][2]
+  const BucketView& b = p.b;
+  const int L = b.L, N = b.N;
+  for (int t = threadIdx.x; t < 2 * L; t += blockDim.x) sh_phase[t] = p.phase[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int unit = blockIdx.x * (kMeasureThreads / 32) + warp;
+  if (unit >= n_units) return;
+  const MeasureUnit m = measure_unit<V>(p, unit);
+  const size_t plane = static_cast<size_t>(N) * V;
+
+  double acc[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
+  float part[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) part[q] = 0.0f;
+  int batch = 0;
+  for (int i = lane; i < N; i += 32) {
+    measure_site<V, PREC>(b.J, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
+    if (++batch == 8) {
+#pragma unroll
+      for (int qq = 0; qq < kNQ; ++qq) {
+        acc[qq] += static_cast<double>(part[qq]);
+        part[qq] = 0.0f;
+      }
+      batch = 0;
+    }
+  }
+  double mine = 0.0;
+#pragma unroll
+  for (int qq = 0; qq < kNQ; ++qq) {
+    const double d = warp_sum(acc[qq] + static_cast<double>(part[qq]));
+    if (lane == qq) mine = d;
+  }
+  if (lane < kNQ) p.partial[static_cast<size_t>(unit) * kNQ + lane] = mine;
 }
 
 // Turns the raw sums of one bucket into the accumulated observables:

@@ -158,10 +158,13 @@ def _oracle_measure(lat, J, st, E):
     return obs
 
 
-@pytest.mark.parametrize("layout", [hsg.PLAIN, hsg.BATCHED])
-def test_measurement_matches_oracle(layout):
+@pytest.mark.parametrize("layout,Ls", [(hsg.PLAIN, [12, 8]), (hsg.BATCHED, [12, 8]),
+                                       (hsg.BATCHED, [16, 8])])
+def test_measurement_matches_oracle(layout, Ls):
+    """Small lattices (N < 4096) are measured one warp per replica pair, L=16
+    by blocks over chunks of sites."""
     betas = [0.0, 0.8, 3.0]
-    lat, J = make([12, 8], betas, n_rep=4, prec=hsg.F16, layout=layout)
+    lat, J = make(Ls, betas, n_rep=4, prec=hsg.F16, layout=layout)
     lat.run_steps(4)
     lat.reset_observables()
     lat.measure()
