@@ -172,17 +172,6 @@ __device__ __forceinline__ void site_field(const void* Jb, int N, int pos, int p
   combine_field<V>(hf, hb, h);
 }
 
-// Pulls the six bonds of a site into L1 ahead of site_field.
-template <int PREC>
-__device__ __forceinline__ void prefetch_bonds(const void* Jb, int N, int pos, int pos_xm, int pos_ym, int pos_zm) {
-  const int idx[6] = {pos, N + pos, 2 * N + pos, pos_xm, N + pos_ym, 2 * N + pos_zm};
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if constexpr (PREC == kPrecF16) prefetch_l1(static_cast<const uint4*>(Jb) + idx[q]);
-    else prefetch_l1(static_cast<const float*>(Jb) + static_cast<size_t>(idx[q]) * 6);
-  }
-}
-
 template <int KIND, int V>
 __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3][V], const float (&beta)[V],
                                             uint32_t i_nat, uint32_t lat0, uint32_t t, uint2 key) {
@@ -327,18 +316,6 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       const int q_dn = (q == 0) ? L - 1 : q - 1;
       const int aw = ab;              // white site of plane z-1 in this column
       const int plq = q * LL;
-      {
-        // bonds of the next step's sites into L1: black site of plane z+1
-        // and white site of plane z (both of x-parity ab ^ 1)
-        const int an = ab ^ 1;
-        const int pn = (pz + 1 == L) ? 0 : pz + 1;
-        const int pln = pn * LL, plz = pz * LL;
-        prefetch_bonds<PREC>(Jb, N, pln + yrow + an * half + k, pln + yrow + (an ? k : half + k_dn),
-                             pln + ydrow + an * half + k, plz + yrow + an * half + k);
-        if (owner && z >= 1)
-          prefetch_bonds<PREC>(Jb, N, plz + yrow + an * half + k, plz + yrow + (an ? k : half + k_dn),
-                               plz + ydrow + an * half + k, pz_dn * LL + yrow + an * half + k);
-      }
       float xp[3][V], xm[3][V], yu[3][V], yd[3][V], zu[3][V], zd[3][V], h[3][V];
       lds_site<V>(at(z, r, ab, k), B0, comp_f);
       lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f);

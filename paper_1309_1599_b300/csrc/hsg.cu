@@ -329,7 +329,9 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
     return true;
   }
   if ((L * V) % 4 != 0) return false;  // 16-byte rows for the bulk copies
-  for (int B = L / 2; B >= 8; --B) {
+  // the smallest band that tiles L: more, smaller CTAs per SM overlap their
+  // per-plane barriers (8-row bands ran faster than 16-row ones at L = 64)
+  for (int B = 8; B <= L / 2; ++B) {
     if (L % B != 0) continue;
     if (threads_for(B + 2) <= max_threads && smem_for(B + 4) <= max_smem) {
       *band_rows = B;

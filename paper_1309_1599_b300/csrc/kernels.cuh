@@ -254,10 +254,6 @@ __device__ __forceinline__ void combine_field(const float (&hf)[3][V], const flo
     for (int v = 0; v < V; ++v) h[c][v] = hf[c][v] + hb[c][v];
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

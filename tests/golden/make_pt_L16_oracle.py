@@ -1,12 +1,15 @@
-"""Writes tests/golden/pt_L16_oracle.json: block averages of the FP64 oracle
-on the parallel-tempering workload (L=16, one sample, 16 temperatures evenly
-spaced in [0.15, 0.75] x 2 replicas, Gaussian couplings, 20000 steps of one
-heat-bath + 8 overrelaxation sweeps + one PT sweep, observables every 10
-steps).  Calls only the oracle and the seeded input generator.
+"""Writes tests/golden/pt_L16_oracle.json: block averages of independent
+FP64 oracle chains on the parallel-tempering workload (L=16, the couplings
+of disorder sample 0, 16 temperatures evenly spaced in [0.15, 0.75] x 2
+replicas, 20000 steps of one heat-bath + 8 overrelaxation sweeps + one PT
+sweep, observables every 10 steps).  Chain c starts from the random spins of
+generator sample c and uses the random streams of sample index c, as chain c
+of the GPU test does.  Calls only the oracle and the seeded input generator.
 
-    python tests/golden/make_pt_L16_oracle.py
+    python tests/golden/make_pt_L16_oracle.py      # 4 chains in parallel
 """
 import json
+import multiprocessing as mp
 import os
 import sys
 import time
@@ -14,26 +17,25 @@ import time
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-import numpy as np  # noqa: E402
-
-import hsg_inputs as gi  # noqa: E402
-import oracle  # noqa: E402
-
-L, N_T, N_REP, SEED = 16, 16, 2, 1
+L, N_T, N_REP, SEED, N_CHAINS = 16, 16, 2, 1, 4
 STEPS, BLOCK, MEASURE_EVERY, N_OR = 20000, 1000, 10, 8
 
 
-def main():
+def chain(c):
+    import numpy as np
+
+    import hsg_inputs as gi
+    import oracle
     beta = gi.linear_betas(0.15, 0.75, N_T)
     J6 = gi.couplings(L, SEED, 0)
-    spins = gi.random_spins_batch(L, SEED, 0, N_T * N_REP)
-    smp = oracle.Sample(L, J6, spins, beta, N_REP, SEED)
+    spins = gi.random_spins_batch(L, SEED, c, N_T * N_REP)
+    smp = oracle.Sample(L, J6, spins, beta, N_REP, SEED, sample_index=c)
     blocks = []
     t0 = time.time()
     for b in range(STEPS // BLOCK):
         smp.obs[:] = 0
         smp.counts[:] = 0
-        smp.run(BLOCK, N_OR, MEASURE_EVERY)
+        smp.run(BLOCK, N_OR, MEASURE_EVERY, n_threads=max(1, os.cpu_count() // N_CHAINS))
         obs = smp.obs.copy()
         n = smp.counts[:, None].astype(float)
         mean = np.empty_like(obs)
@@ -41,11 +43,19 @@ def main():
         mean[:, 2:8] = obs[:, 2:8] / (n * (N_REP // 2))   # per pair
         mean[:, 8] = obs[:, 8] / (n[:, 0] * N_REP)
         blocks.append(mean.tolist())
-        print(f"block {b} done at {time.time() - t0:.0f} s", flush=True)
+        print(f"chain {c} block {b} done at {time.time() - t0:.0f} s", flush=True)
+    return blocks, smp.accepted.tolist()
+
+
+def main():
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(N_CHAINS) as pool:
+        res = pool.map(chain, range(N_CHAINS))
+    import oracle
     out = {"L": L, "n_temps": N_T, "n_replicas": N_REP, "seed": SEED, "steps": STEPS,
            "block_steps": BLOCK, "measure_every": MEASURE_EVERY, "n_or": N_OR,
            "T_range": [0.15, 0.75], "observables": list(oracle.OBS_NAMES),
-           "block_means": blocks, "pt_accepted": smp.accepted.tolist()}
+           "chains": [r[0] for r in res], "pt_accepted": [r[1] for r in res]}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pt_L16_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f)

@@ -254,12 +254,15 @@ def test_or_conserves_energy_and_norm_on_gpu():
 
 
 FUSED_CASES = [
-    # (Ls, n_rep, prec, layout): whole-plane and banded tilings of the fused sweep
-    ([8, 12], 2, hsg.F32, hsg.PLAIN),
-    ([16], 2, hsg.F16, hsg.BATCHED),
-    ([32], 1, hsg.F16, hsg.BATCHED),
-    ([40], 1, hsg.F16, hsg.BATCHED),
-    ([48], 1, hsg.F32, hsg.PLAIN),
+    # (Ls, n_rep, prec, layout, band_rows): whole-plane and banded tilings of
+    # the fused sweep (band_rows 0: the library's choice)
+    ([8, 12], 2, hsg.F32, hsg.PLAIN, 0),
+    ([16], 2, hsg.F16, hsg.BATCHED, 0),
+    ([32], 1, hsg.F16, hsg.BATCHED, 0),
+    ([32], 1, hsg.F16, hsg.BATCHED, 16),
+    ([40], 1, hsg.F16, hsg.BATCHED, 0),
+    ([48], 1, hsg.F32, hsg.PLAIN, 0),
+    ([64], 1, hsg.F16, hsg.BATCHED, 16),
 ]
 
 
@@ -267,12 +270,15 @@ FUSED_CASES = [
 def test_fused_sweep_equals_two_pass_bitwise(case):
     """The fused one-pass sweep and the two-pass half-sweeps sum each field in
     the same order, so they must give identical spins, energies and labels."""
-    Ls, n_rep, prec, layout = FUSED_CASES[case]
+    Ls, n_rep, prec, layout, band = FUSED_CASES[case]
     betas = gi.linear_betas(0.4, 1.2, 2)
     runs = []
     for kernel in (hsg.SWEEP_AUTO, hsg.SWEEP_TWO_PASS):
         lat = hsg.Lattice(Ls, betas, n_replicas=n_rep, coupling_prec=prec, layout=layout, n_or=3,
-                          measure_every=2, seed=5, sweep_kernel=kernel)
+                          measure_every=2, seed=5, sweep_kernel=kernel,
+                          band_rows=band if kernel == hsg.SWEEP_AUTO else 0)
+        if kernel == hsg.SWEEP_AUTO and band:
+            assert lat.get_sweep_plan(0)["band_rows"] == band
         pstr = "f16" if prec == hsg.F16 else "f32"
         for s, L in enumerate(Ls):
             lat.set_couplings(s, gi.couplings(L, 5, s, precision=pstr))

@@ -2,10 +2,16 @@
 parity at the full size of the throughput workload (sampled lattices).
 
 Trajectories under identical random streams separate after a few sweeps
-(overrelaxation is chaotic), so after that the GPU run and the oracle run are
-independent realisations of the same Markov chain.  Their long-run averages
-must agree within 3 sigma, sigma from the spread of block averages (binning)
-of each run.
+(overrelaxation is chaotic), and at low temperature a single chain's time
+average depends on the valley it settles in, so one chain's binning error
+does not describe the spread between runs.  The long-run averages are
+therefore compared between ensembles of independent chains of the same
+Markov chain -- same couplings, independent initial spins and random streams
+-- with the pooled-variance two-sample t statistic; under the hypothesis
+that GPU and oracle sample the same process it is ~N(0,1) at any time,
+equilibrated or not.  Threshold: |t| < 3 per observable (north_star: "within
+3 sigma"), with a 4-sigma bound where many temperatures are compared at
+once, plus a bound on the mean of t^2.
 """
 import json
 import os
@@ -32,87 +38,90 @@ def _block_means(obs, counts, n_rep):
     return m
 
 
-def _mean_err(blocks):
-    b = np.asarray(blocks)
-    return b.mean(0), b.std(0, ddof=1) / np.sqrt(len(b))
+def _t_stat(a, b):
+    """Pooled two-sample t statistic along axis 0 of chain averages a, b."""
+    a, b = np.asarray(a), np.asarray(b)
+    na, nb = len(a), len(b)
+    va, vb = a.var(0, ddof=1), b.var(0, ddof=1)
+    sp2 = ((na - 1) * va + (nb - 1) * vb) / (na + nb - 2)
+    return (a.mean(0) - b.mean(0)) / np.sqrt(sp2 * (1.0 / na + 1.0 / nb) + 1e-300)
+
+
+def _gpu_chains(L, beta, n_rep, n_chains, steps, measure_every, layout, seed=1):
+    """n_chains independent chains on the couplings of generator sample 0:
+    chain c = context sample c (its own initial spins and random streams)."""
+    lat = hsg.Lattice([L] * n_chains, beta, n_replicas=n_rep, coupling_prec=hsg.F32,
+                      layout=layout, n_or=8, measure_every=measure_every, seed=seed)
+    J6 = gi.couplings(L, seed, 0)
+    for c in range(n_chains):
+        lat.set_couplings(c, J6)
+        for j in range(lat.R):
+            lat.set_spins(c, j, gi.random_spins(L, seed, c, j))
+    return lat, J6
 
 
 def test_long_run_L8_single_temperature_matches_oracle():
     """Plain FP32 form, L=8, T=0.5, 2 replicas, 1 HB + 8 OR per step,
-    observables every step: 1000 steps on both sides, 20 blocks of 50,
-    the first 4 blocks discarded."""
-    L, beta, seed = 8, 2.0, 1
-    J6 = gi.couplings(L, seed, 0)
-    spins = gi.random_spins_batch(L, seed, 0, 2)
-    lat = hsg.Lattice(L, [beta], n_replicas=2, coupling_prec=hsg.F32, layout=hsg.PLAIN, n_or=8,
-                      measure_every=1, seed=seed)
-    lat.set_couplings(0, J6)
-    for j in range(2):
-        lat.set_spins(0, j, spins[j])
-    smp = oracle.Sample(L, J6, spins, [beta], 2, seed)
-    gpu, cpu = [], []
-    for b in range(20):
-        lat.reset_observables()
-        lat.run_steps(50)
-        o, c = lat.read_observables()
-        gpu.append(_block_means(o[0, 0], c[0, 0], 2))
-        smp.obs[:] = 0
-        smp.counts[:] = 0
-        smp.run(50, 8, 1)
+    observables every step, 1000 steps: averages over steps 201-1000 of 32
+    GPU chains against 8 oracle chains."""
+    L, beta, seed, steps, skip = 8, 2.0, 1, 1000, 200
+    lat, J6 = _gpu_chains(L, [beta], 2, 32, steps, 1, hsg.PLAIN, seed)
+    lat.run_steps(skip)
+    lat.reset_observables()
+    lat.run_steps(steps - skip)
+    o, c = lat.read_observables()
+    gpu = _block_means(o[:, 0], c[:, 0], 2)                  # [chain, obs]
+    cpu = []
+    for ch in range(8):
+        smp = oracle.Sample(L, J6, gi.random_spins_batch(L, seed, ch, 2), [beta], 2, seed,
+                            sample_index=ch)
+        smp.run(skip, 8, 0)
+        smp.run(steps - skip, 8, 1)
         cpu.append(_block_means(smp.obs[0], smp.counts[0], 2))
-    mg, eg = _mean_err(gpu[4:])
-    mc, ec = _mean_err(cpu[4:])
+    t = _t_stat(gpu, cpu)
     for j, name in [(0, "e"), (2, "q2"), (5, "c2")]:
-        z = (mg[j] - mc[j]) / np.sqrt(eg[j] ** 2 + ec[j] ** 2)
-        assert abs(z) < 3, (name, mg[j], mc[j], z)
-    # the chains did separate: the comparison is statistical, not trivial
-    assert not np.allclose(lat.get_spins(0, 0), smp.spins[0], atol=1e-3)
+        assert abs(t[j]) < 3, (name, np.mean(np.asarray(gpu)[:, j]), np.mean(np.asarray(cpu)[:, j]), t[j])
+    # a real comparison: the chains differ and the observable is resolved
+    assert np.asarray(gpu)[:, 0].std() > 0
 
 
 def test_parallel_tempering_L16_matches_stored_oracle():
-    """L=16, one sample, 16 temperatures evenly spaced in [0.15, 0.75] x 2
-    replicas, 20000 steps of HB + 8 OR + PT, observables every 10 steps.
-    The oracle's block averages were stored by tests/golden/make_pt_L16_oracle.py.
-    Means over the last 10 blocks of 1000 steps agree per temperature and
-    observable: |z| < 4 everywhere (16 temperatures x 4 observables) and
-    mean z^2 below 2.5; energies, which equilibrate fastest, within 3 sigma."""
+    """L=16, the couplings of sample 0, 16 temperatures evenly spaced in
+    [0.15, 0.75] x 2 replicas, 20000 steps of HB + 8 OR + PT, observables
+    every 10 steps.  Averages over the second half of 16 GPU chains against
+    the 4 oracle chains stored by tests/golden/make_pt_L16_oracle.py, for
+    e, q2, q2(k_min) and q2_CG at every temperature (64 statistics): all
+    |t| < 4 and mean t^2 < 2; the energies |t| < 3."""
     with open(os.path.join(HERE, "golden", "pt_L16_oracle.json")) as f:
         ref = json.load(f)
     L, NT, n_rep, seed = ref["L"], ref["n_temps"], ref["n_replicas"], ref["seed"]
     beta = gi.linear_betas(*ref["T_range"], NT)
-    lat = hsg.Lattice(L, beta, n_replicas=n_rep, coupling_prec=hsg.F32, layout=hsg.BATCHED,
-                      n_or=ref["n_or"], measure_every=ref["measure_every"], seed=seed)
-    lat.set_couplings(0, gi.couplings(L, seed, 0))
-    for j in range(lat.R):
-        lat.set_spins(0, j, gi.random_spins(L, seed, 0, j))
-    gpu = []
-    for b in range(ref["steps"] // ref["block_steps"]):
-        lat.reset_observables()
-        lat.run_steps(ref["block_steps"])
-        o, c = lat.read_observables()
-        gpu.append(_block_means(o[0], c[0], n_rep))
-    keep = slice(len(gpu) // 2, None)
-    mg, eg = _mean_err(gpu[keep])
-    mc, ec = _mean_err(np.asarray(ref["block_means"])[keep])
-    zs = []
-    for j in (0, 2, 4, 5):                       # e, q2, q2(k_min), q2_CG
-        z = (mg[:, j] - mc[:, j]) / np.sqrt(eg[:, j] ** 2 + ec[:, j] ** 2)
-        zs.append(z)
-        if j == 0:
-            assert np.all(np.abs(z) < 3), z
-    zs = np.concatenate(zs)
-    assert np.all(np.abs(zs) < 4), zs
-    assert np.mean(zs ** 2) < 2.5, np.mean(zs ** 2)
-    # Schwinger-Dyson identity (App. A.4.3) at the higher temperatures
-    hot = slice(0, NT // 2)                      # smallest beta = highest T
-    z_sd = mg[hot, 8] / eg[hot, 8]
+    steps, block = ref["steps"], ref["block_steps"]
+    lat, _ = _gpu_chains(L, beta, n_rep, 16, steps, ref["measure_every"], hsg.BATCHED, seed)
+    lat.run_steps(steps // 2)
+    lat.reset_observables()
+    lat.run_steps(steps // 2)
+    o, c = lat.read_observables()
+    gpu = _block_means(o, c, n_rep)                           # [chain, T, obs]
+    ch = np.asarray(ref["chains"])                            # [chain, block, T, obs]
+    cpu = ch[:, ch.shape[1] // 2:].mean(axis=1)               # equal-size blocks
+    t = _t_stat(gpu, cpu)                                     # [T, obs]
+    assert np.all(np.abs(t[:, 0]) < 3), t[:, 0]
+    tt = t[:, [0, 2, 4, 5]]
+    assert np.all(np.abs(tt) < 4), tt
+    assert np.mean(tt ** 2) < 2.0, np.mean(tt ** 2)
+    # Schwinger-Dyson identity (App. A.4.3) at the high temperatures, where
+    # the chains equilibrate: the chain average vanishes within its error
+    hot = slice(0, NT // 2)                                   # smallest beta = highest T
+    sd = np.asarray(gpu)[:, hot, 8]
+    z_sd = sd.mean(0) / (sd.std(0, ddof=1) / np.sqrt(len(sd)))
     assert np.all(np.abs(z_sd) < 4), z_sd
 
 
 def test_full_size_throughput_workload_sampled_parity():
     """The launch configuration bench.py times (L=64, 8 samples x 64
     lattices, FP16 couplings, two lattices per element, fused sweep in bands
-    of 16 rows): one heat-bath and one overrelaxation sweep from the initial
+    of 8 rows): one heat-bath and one overrelaxation sweep from the initial
     state, checked per half-sweep on whole sampled lattices, plus the fused
     energies and one PT sweep against the oracle."""
     L, S, NT, n_rep, seed = 64, 8, 32, 2, 1
@@ -120,7 +129,7 @@ def test_full_size_throughput_workload_sampled_parity():
     lat = hsg.Lattice([L] * S, beta, n_replicas=n_rep, coupling_prec=hsg.F16, layout=hsg.BATCHED,
                       n_or=8, measure_every=10, seed=seed)
     plan = lat.get_sweep_plan(0)
-    assert plan["fused"] and plan["band_rows"] == 16
+    assert plan["fused"] and plan["band_rows"] == 8
     J = [gi.couplings(L, seed, s, precision="f16") for s in range(S)]
     for s in range(S):
         lat.set_couplings(s, J[s])
@@ -147,7 +156,7 @@ def test_full_size_throughput_workload_sampled_parity():
                 # frame-ambiguous sites (field at the equator h_z = 0) excepted
                 h = oracle.fields(L, J9, before[(s, slot)], 0) + oracle.fields(L, J9, mixed, 1)
                 amb = np.abs(h[:, 2]) < 1e-4 * np.linalg.norm(h, axis=1)
-                assert amb.sum() <= 3
+                assert amb.mean() < 3e-4          # expected fraction 1e-4
                 diff = diff[~amb]
             assert diff.max() <= SWEEP_TOL, ((s, slot), kind, diff.max())
     # energies fused into that overrelaxation sweep, and one PT sweep
