@@ -25,10 +25,12 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["couplings", "ferromagnet", "random_spins", "random_spins_batch",
-           "linear_betas", "geometric_betas", "STREAM_COUPLINGS", "STREAM_SPINS"]
+           "linear_betas", "geometric_betas", "STREAM_COUPLINGS", "STREAM_SPINS", "bimodal_bits",
+           "STREAM_BIMODAL"]
 
 STREAM_COUPLINGS = 0x4A000000
 STREAM_SPINS = 0x53000000
+STREAM_BIMODAL = 0x42000000
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
@@ -62,6 +64,16 @@ def couplings(L: int, seed: int = 1, sample: int = 0, law: str = "gaussian",
     J6 = d.copy()
     J6[..., 0:3] += eps[..., None]
     return _round(J6, precision)
+
+
+def bimodal_bits(L: int, seed: int = 1, sample: int = 0) -> np.ndarray:
+    """Bimodal couplings of disorder sample `sample` as their sign bytes,
+    uint8 [L^3, 3]: seven independent fair bits per bond (bit 0 for the
+    isotropic coupling, bits 1..6 for the six anisotropy entries), bit 7
+    clear."""
+    N = L ** 3
+    g = _rng(seed, STREAM_BIMODAL + sample)
+    return g.integers(0, 128, (N, 3), dtype=np.uint8)
 
 
 def ferromagnet(L: int) -> np.ndarray:

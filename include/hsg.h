@@ -60,7 +60,9 @@ typedef enum {
 
 /* Storage precision of the couplings on the device.  Values are rounded once
  * (round to nearest even) from the float32 host array. */
-enum { HSG_F32 = 0, HSG_F16 = 1 };
+/* Coupling storage: FP32, FP16, or bimodal (Sec. II.A: J = +-1 and
+ * D^ab = +-D, one byte per bond holding the seven signs). */
+enum { HSG_F32 = 0, HSG_F16 = 1, HSG_BIMODAL = 2 };
 
 /* Device spin layout.
  *   HSG_LAYOUT_PLAIN    one lattice per thread; each lattice reads its own
@@ -99,7 +101,7 @@ typedef struct {
   int n_replicas;         /* >= 1 */
   int n_temps;            /* N_T >= 1 */
   const double *beta;     /* [N_T] inverse temperatures, >= 0, increasing */
-  int coupling_prec;      /* HSG_F32 or HSG_F16 */
+  int coupling_prec;      /* HSG_F32, HSG_F16 or HSG_BIMODAL */
   int layout;             /* HSG_LAYOUT_PLAIN or HSG_LAYOUT_BATCHED */
   int n_or;               /* overrelaxation sweeps per step, >= 0 */
   int measure_every;      /* hsg_run_steps measures every this many steps (0: never) */
@@ -119,6 +121,9 @@ typedef struct {
                              the layout's lattices per element, and
                              12 N_T L^3 bytes <= 224 KiB for every L
                              (HSG_EINVAL otherwise).  0: streaming steps. */
+  double bimodal_D;       /* HSG_BIMODAL: the magnitude D >= 0 of the
+                             anisotropic couplings (the paper uses 0.5 and 1);
+                             ignored by the other formats */
 } hsg_config;
 
 /* Create a context: validates cfg (copied; the caller's arrays may be freed
@@ -137,8 +142,21 @@ void hsg_destroy(hsg_t h);
  * Invalidates the stored energies. */
 hsg_status hsg_set_couplings(hsg_t h, int sample, const float *J6);
 
-/* The stored couplings of one sample as float32 [N][3][6] (exact values). */
+/* The stored couplings of one sample as float32 [N][3][6] (exact values;
+ * for HSG_BIMODAL the decoded matrices, computed in FP32 as below). */
 hsg_status hsg_get_couplings(hsg_t h, int sample, float *J6_out);
+
+/* Bimodal couplings of one sample (Sec. II.A), for contexts created with
+ * HSG_BIMODAL: host uint8 [N][3], natural site order, one byte per bond
+ * (i, i+e_mu).  Bit 0 is the sign of the isotropic coupling J = +-1, bits 1-6
+ * the signs of D^xx, D^yy, D^zz, D^xy, D^xz, D^yz = +-D (a set bit means
+ * negative), bit 7 must be 0.  The kernels use the entries
+ * (J + D^xx, J + D^yy, J + D^zz, D^xy, D^xz, D^yz), each sum rounded to FP32.
+ * HSG_EINVAL if the context is not bimodal or a bit 7 is set (nothing
+ * stored).  hsg_set_couplings returns HSG_EINVAL on a bimodal context: the
+ * signs cannot be recovered from the matrices when D = 1. */
+hsg_status hsg_set_couplings_bimodal(hsg_t h, int sample, const uint8_t *bits);
+hsg_status hsg_get_couplings_bimodal(hsg_t h, int sample, uint8_t *bits_out);
 
 /* Spins of one lattice slot from / to host float32 [N][3].  Spins are stored
  * as given (no normalisation). */
@@ -263,7 +281,7 @@ const char *hsg_last_error(void);
 
 /* ABI version of this header. */
 int hsg_version(void);
-#define HSG_VERSION 1
+#define HSG_VERSION 2  /* bumped with every change of hsg_config or of a signature */
 
 #ifdef __cplusplus
 }

@@ -99,6 +99,7 @@ def _load():
                 "oracle_two_site_chain": (None, [vp, d, u64, u32, ctypes.c_long,
                                                  ctypes.c_long, vp, vp, vp]),
                 "oracle_fields": (None, [i32, vp, vp, i32, vp]),
+                "oracle_bimodal_j9": (None, [ctypes.c_long, vp, d, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -160,6 +161,16 @@ def hb_words(seed: int, site: int, lattice: int, t: int):
 # --------------------------------------------------------------------------
 # Couplings
 # --------------------------------------------------------------------------
+def bimodal_j9(bits, D: float) -> np.ndarray:
+    """Bimodal couplings (Sec. II.A) from their bytes uint8 [N,3] (bit 0: sign
+    of J = +-1; bits 1..6: signs of D^xx, D^yy, D^zz, D^xy, D^xz, D^yz = +-D)
+    as general 3x3 matrices [N,3,9] in float64."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    out = np.empty(bits.shape + (9,), dtype=np.float64)
+    _load().oracle_bimodal_j9(bits.size, _ptr(bits), float(D), _ptr(out))
+    return out
+
+
 def j9_from_j6(J6) -> np.ndarray:
     """Expand symmetric couplings [N,3,6] (xx,yy,zz,xy,xz,yz) to general
     3x3 matrices [N,3,9] in float64 (exact: float32 -> float64)."""

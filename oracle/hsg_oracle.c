@@ -185,6 +185,24 @@ void oracle_local_field(int L, const double *J9, const double *s, long i,
   }
 }
 
+/* Bimodal couplings (Sec. II.A): the isotropic coupling J = +-1 and the six
+   independent entries D^{ab} (a >= b) of the symmetric anisotropy = +-D.
+   One byte per bond: bit 0 is the sign of J, bits 1..6 the signs of
+   D^xx, D^yy, D^zz, D^xy, D^xz, D^yz (a set bit means negative).  Writes the
+   bond matrix J I + D as a general 3x3, row-major. */
+void oracle_bimodal_j9(long n_bonds, const unsigned char *bits, double D, double *J9) {
+  for (long k = 0; k < n_bonds; ++k) {
+    unsigned v = bits[k];
+    double iso = (v & 1u) ? -1.0 : 1.0;
+    double d[6];
+    for (int e = 0; e < 6; ++e) d[e] = ((v >> (e + 1)) & 1u) ? -D : D;
+    double *M = J9 + k * 9;
+    M[0] = iso + d[0]; M[1] = d[3];       M[2] = d[4];
+    M[3] = d[3];       M[4] = iso + d[1]; M[5] = d[5];
+    M[6] = d[4];       M[7] = d[5];       M[8] = iso + d[2];
+  }
+}
+
 /* Energy, Eq. (1): each nearest-neighbour bond counted once. */
 double oracle_energy(int L, const double *J9, const double *s) {
   long N = (long)L * L * L;

@@ -20,7 +20,8 @@ __all__ = ["Lattice", "HsgError", "load_library", "philox4x32_10", "library_path
            "F32", "F16", "PLAIN", "BATCHED", "SWEEP_AUTO", "SWEEP_TWO_PASS", "NOBS",
            "OBS_NAMES"]
 
-F32, F16 = 0, 1
+ABI_VERSION = 2            # HSG_VERSION of include/hsg.h
+F32, F16, BIMODAL = 0, 1, 2
 PLAIN, BATCHED = 0, 1
 SWEEP_AUTO, SWEEP_TWO_PASS = 0, 1
 NOBS = 9
@@ -50,13 +51,16 @@ class _Config(ctypes.Structure):
                 ("layout", ctypes.c_int), ("n_or", ctypes.c_int), ("measure_every", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int),
-                ("band_rows", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("band_rows", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("bimodal_D", ctypes.c_double)]
 
 
 _SIGNATURES = {
     "hsg_lattice_create": [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_void_p)],
     "hsg_set_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_set_couplings_bimodal": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_couplings_bimodal": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_set_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_sweep_hb": [ctypes.c_void_p, ctypes.c_int],
@@ -102,6 +106,9 @@ def load_library():
         lib.hsg_last_error.restype = ctypes.c_char_p
         lib.hsg_version.argtypes = []
         lib.hsg_version.restype = ctypes.c_int
+        if lib.hsg_version() != ABI_VERSION:
+            raise ImportError(f"{_LIB_PATH} has ABI version {lib.hsg_version()}, this binding "
+                              f"expects {ABI_VERSION}: rebuild it")
         _lib = lib
     return _lib
 
@@ -145,7 +152,8 @@ class Lattice:
 
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
-                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0, persistent=False):
+                 timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0, persistent=False,
+                 bimodal_D=1.0):
         lib = load_library()
         _require_gpu()
         if np.isscalar(L):
@@ -175,6 +183,9 @@ class Lattice:
         cfg.sweep_kernel = int(sweep_kernel)
         cfg.band_rows = int(band_rows)
         cfg.persistent = 1 if persistent else 0
+        cfg.bimodal_D = float(bimodal_D)
+        self.coupling_prec = int(coupling_prec)
+        self.bimodal_D = float(bimodal_D)
         h = ctypes.c_void_p()
         _check(lib.hsg_lattice_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -210,6 +221,16 @@ class Lattice:
     def get_couplings(self, sample: int) -> np.ndarray:
         out = np.empty((self.N(sample), 3, 6), dtype=np.float32)
         _check(self._lib.hsg_get_couplings(self._h, sample, _ptr(out)))
+        return out
+
+    def set_couplings_bimodal(self, sample: int, bits) -> None:
+        bits = np.ascontiguousarray(bits, dtype=np.uint8)
+        assert bits.size == self.N(sample) * 3
+        _check(self._lib.hsg_set_couplings_bimodal(self._h, sample, _ptr(bits)))
+
+    def get_couplings_bimodal(self, sample: int) -> np.ndarray:
+        out = np.empty((self.N(sample), 3), dtype=np.uint8)
+        _check(self._lib.hsg_get_couplings_bimodal(self._h, sample, _ptr(out)))
         return out
 
     def set_spins(self, sample: int, slot: int, s) -> None:

@@ -54,6 +54,7 @@ struct FusedParams {
   int* status;            // device status word
   long long timeout;      // clock64 cycles for one wait
   int probe_timeout;      // nonzero: first wait on a barrier nobody completes
+  float D;                // bimodal couplings: magnitude of the anisotropy
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -150,24 +151,24 @@ __device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) 
 // of the site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds
 // are this site's -x, -y, -z bonds).
 template <int V, int PREC>
-__device__ __forceinline__ void site_field(const void* Jb, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
+__device__ __forceinline__ void site_field(const void* Jb, float D, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
                                            const float (&xp)[3][V], const float (&xm)[3][V],
                                            const float (&yu)[3][V], const float (&yd)[3][V],
                                            const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V]) {
   float hf[3][V], hb[3][V], j[6];
   zero3<V>(hf);
   zero3<V>(hb);
-  load_bond<PREC>(Jb, pos, j);
+  load_bond<PREC>(Jb, pos, j, D);
   add_bond<V>(j, xp, hf);
-  load_bond<PREC>(Jb, N + pos, j);
+  load_bond<PREC>(Jb, N + pos, j, D);
   add_bond<V>(j, yu, hf);
-  load_bond<PREC>(Jb, 2 * N + pos, j);
+  load_bond<PREC>(Jb, 2 * N + pos, j, D);
   add_bond<V>(j, zu, hf);
-  load_bond<PREC>(Jb, pos_xm, j);
+  load_bond<PREC>(Jb, pos_xm, j, D);
   add_bond<V>(j, xm, hb);
-  load_bond<PREC>(Jb, N + pos_ym, j);
+  load_bond<PREC>(Jb, N + pos_ym, j, D);
   add_bond<V>(j, yd, hb);
-  load_bond<PREC>(Jb, 2 * N + pos_zm, j);
+  load_bond<PREC>(Jb, 2 * N + pos_zm, j, D);
   add_bond<V>(j, zd, hb);
   combine_field<V>(hf, hb, h);
 }
@@ -224,9 +225,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   float* out_g = p.out + gbase;
   const size_t plane_g = static_cast<size_t>(N) * V;   // component stride in global memory
   // couplings of this sample (element size depends on the storage precision)
-  const void* Jb = (PREC == kPrecF16)
-                       ? static_cast<const void*>(static_cast<const uint4*>(p.J) + static_cast<size_t>(sb) * 3 * N)
-                       : static_cast<const void*>(static_cast<const float*>(p.J) + static_cast<size_t>(sb) * 3 * N * 6);
+  const void* Jb = sample_bonds<PREC>(p.J, sb, N);
   const bool want_energy = (p.e_partial != nullptr);
   const int LL = L * L;
   const int yrow = y * L, ydrow = y_dn * L;
@@ -326,7 +325,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       lds_site<V>(at(z - 1, r, ab, k), zd, comp_f);
       {
         const int pl = pz * LL;
-        site_field<V, PREC>(Jb, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
+        site_field<V, PREC>(Jb, p.D, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
                             pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k, xp, xm, yu, yd, zu,
                             zd, h);
       }
@@ -342,7 +341,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
         lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k : k_dn), xm, comp_f);
         lds_site<V>(at(z - 1, r_up, aw, k), yu, comp_f);
         lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
-        site_field<V, PREC>(Jb, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
+        site_field<V, PREC>(Jb, p.D, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
                             plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k, xp, xm, yu, yd, B0,
                             Bm2, h);
         const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));

@@ -43,7 +43,7 @@ struct Bucket {
   int* d_samples = nullptr;
   float* d_spins[2] = {nullptr, nullptr};  // [S_b][G][3][N][V]; [1] only with the fused sweep
   int cur = 0;                // which of d_spins holds the current spins
-  void* d_J = nullptr;        // f32 [S_b][3][N][6] or f16 [S_b][3][N][8]
+  void* d_J = nullptr;        // f32 [S_b][3][N][6], f16 [S_b][3][N][8] or bimodal u8 [S_b][3][N]
   int sweep_chunks = 0;       // blocks per lattice group in a half-sweep
   bool fused = false;         // sweeps use k_sweep_fused (ping-pong buffers)
   int band_rows = 0, n_bands = 0;  // fused-sweep tiling
@@ -66,6 +66,7 @@ void hsg_record_error(const std::string& msg) { g_last_error = msg; }
 
 struct hsg_ctx {
   int S = 0, n_rep = 0, NT = 0, R = 0, V = 1, prec = HSG_F32, layout = 0, n_or = 0;
+  float bimodal_D = 0.0f;      // HSG_BIMODAL: magnitude of the anisotropic couplings
   int measure_every = 0;
   uint64_t seed = 0;
   std::vector<int> Ls;
@@ -104,8 +105,24 @@ uint2 philox_key(uint64_t seed) {
   return make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
 }
 
-size_t bond_elems(int prec) { return prec == HSG_F16 ? 8 : 6; }
-size_t bond_bytes(int prec) { return prec == HSG_F16 ? 16 : 24; }
+size_t bond_bytes(int prec) { return prec == HSG_F16 ? 16 : prec == HSG_BIMODAL ? 1 : 24; }
+
+template <int K>
+using IC = std::integral_constant<int, K>;
+
+// Calls f(IC<V>, IC<PREC>) for a context's layout (lattices per element) and
+// coupling format; every branch must return the same type.
+template <typename F>
+decltype(auto) dispatch(int V, int prec, F&& f) {
+  if (V == 2) {
+    if (prec == HSG_F16) return f(IC<2>{}, IC<kPrecF16>{});
+    if (prec == HSG_BIMODAL) return f(IC<2>{}, IC<kPrecBimodal>{});
+    return f(IC<2>{}, IC<kPrecF32>{});
+  }
+  if (prec == HSG_F16) return f(IC<1>{}, IC<kPrecF16>{});
+  if (prec == HSG_BIMODAL) return f(IC<1>{}, IC<kPrecBimodal>{});
+  return f(IC<1>{}, IC<kPrecF32>{});
+}
 
 void free_ctx(hsg_ctx* h) {
   if (!h) return;
@@ -175,6 +192,7 @@ BucketView view(const Bucket& b) {
   v.N = b.N;
   v.S_b = b.S_b;
   v.G = b.G;
+  v.D = 0.0f;
   return v;
 }
 
@@ -182,6 +200,7 @@ template <int KIND>
 hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cudaStream_t st) {
   SweepParams p;
   p.b = view(b);
+  p.b.D = h->bimodal_D;
   p.colour = colour;
   p.chunks = b.sweep_chunks;
   p.R = h->R;
@@ -192,13 +211,10 @@ hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cud
   p.e_partial = energy ? b.d_epart : nullptr;
   const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.sweep_chunks);
   *h->launch_sink += 1;
-  if (h->V == 2) {
-    if (h->prec == HSG_F16) k_sweep_half<KIND, 2, kPrecF16, true><<<grid, kSweepThreads, 0, st>>>(p);
-    else k_sweep_half<KIND, 2, kPrecF32, true><<<grid, kSweepThreads, 0, st>>>(p);
-  } else {
-    if (h->prec == HSG_F16) k_sweep_half<KIND, 1, kPrecF16, true><<<grid, kSweepThreads, 0, st>>>(p);
-    else k_sweep_half<KIND, 1, kPrecF32, true><<<grid, kSweepThreads, 0, st>>>(p);
-  }
+  dispatch(h->V, h->prec, [&](auto v, auto pr) {
+    k_sweep_half<KIND, decltype(v)::value, decltype(pr)::value, true><<<grid, kSweepThreads, 0, st>>>(p);
+    return 0;
+  });
   HSG_CUDA(cudaGetLastError());
   return HSG_OK;
 }
@@ -234,17 +250,15 @@ hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, boo
   p.status = h->d_status;
   p.timeout = timeout > 0 ? timeout : h->timeout_cycles;
   p.probe_timeout = probe_timeout ? 1 : 0;
+  p.D = h->bimodal_D;
   const int rows_t = (b.band_rows == b.L) ? b.L : b.band_rows + 2;
   const unsigned block = static_cast<unsigned>(((rows_t * (b.L / 2)) + 31) / 32 * 32);
   const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.n_bands);
   *h->launch_sink += 1;
-  if (h->V == 2) {
-    if (h->prec == HSG_F16) fused_kernel_launch<KIND, 2, kPrecF16>(p, grid, block, b.fused_smem, st);
-    else fused_kernel_launch<KIND, 2, kPrecF32>(p, grid, block, b.fused_smem, st);
-  } else {
-    if (h->prec == HSG_F16) fused_kernel_launch<KIND, 1, kPrecF16>(p, grid, block, b.fused_smem, st);
-    else fused_kernel_launch<KIND, 1, kPrecF32>(p, grid, block, b.fused_smem, st);
-  }
+  dispatch(h->V, h->prec, [&](auto v, auto pr) {
+    fused_kernel_launch<KIND, decltype(v)::value, decltype(pr)::value>(p, grid, block, b.fused_smem, st);
+    return 0;
+  });
   HSG_CUDA(cudaGetLastError());
   if (!probe_timeout) b.cur ^= 1;
   return HSG_OK;
@@ -270,38 +284,19 @@ int fused_max_threads_one() {
 // Largest block the fused kernels (heat-bath and overrelaxation) can launch
 // with, as the driver reports it for their register use; 0 if unknown.
 int fused_max_threads(int V, int prec) {
-  int a, b;
-  if (V == 2 && prec == HSG_F16) {
-    a = fused_max_threads_one<kHB, 2, kPrecF16>();
-    b = fused_max_threads_one<kOR, 2, kPrecF16>();
-  } else if (V == 2) {
-    a = fused_max_threads_one<kHB, 2, kPrecF32>();
-    b = fused_max_threads_one<kOR, 2, kPrecF32>();
-  } else if (prec == HSG_F16) {
-    a = fused_max_threads_one<kHB, 1, kPrecF16>();
-    b = fused_max_threads_one<kOR, 1, kPrecF16>();
-  } else {
-    a = fused_max_threads_one<kHB, 1, kPrecF32>();
-    b = fused_max_threads_one<kOR, 1, kPrecF32>();
-  }
-  return std::min(std::min(a, b), kFusedMaxThreads);
+  return dispatch(V, prec, [](auto v, auto pr) {
+    constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
+    const int a = fused_max_threads_one<kHB, VV, P>(), b = fused_max_threads_one<kOR, VV, P>();
+    return std::min(std::min(a, b), kFusedMaxThreads);
+  });
 }
 
 hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
-  if (V == 2 && prec == HSG_F16) {
-    HSG_TRY((allow_fused_smem<kHB, 2, kPrecF16>(bytes)));
-    return allow_fused_smem<kOR, 2, kPrecF16>(bytes);
-  }
-  if (V == 2) {
-    HSG_TRY((allow_fused_smem<kHB, 2, kPrecF32>(bytes)));
-    return allow_fused_smem<kOR, 2, kPrecF32>(bytes);
-  }
-  if (prec == HSG_F16) {
-    HSG_TRY((allow_fused_smem<kHB, 1, kPrecF16>(bytes)));
-    return allow_fused_smem<kOR, 1, kPrecF16>(bytes);
-  }
-  HSG_TRY((allow_fused_smem<kHB, 1, kPrecF32>(bytes)));
-  return allow_fused_smem<kOR, 1, kPrecF32>(bytes);
+  return dispatch(V, prec, [&](auto v, auto pr) {
+    constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
+    const hsg_status a = allow_fused_smem<kHB, VV, P>(bytes);
+    return a != HSG_OK ? a : allow_fused_smem<kOR, VV, P>(bytes);
+  });
 }
 
 // Tiling of the fused sweep for lattice size L and V lattices per element:
@@ -366,8 +361,9 @@ void* persistent_fn_js(int js, int L) {
 }
 
 void* persistent_kernel(int V, int prec, int js, int L) {
-  if (V == 2) return prec == HSG_F16 ? persistent_fn_js<2, kPrecF16>(js, L) : persistent_fn_js<2, kPrecF32>(js, L);
-  return prec == HSG_F16 ? persistent_fn_js<1, kPrecF16>(js, L) : persistent_fn_js<1, kPrecF32>(js, L);
+  return dispatch(V, prec, [&](auto v, auto pr) {
+    return persistent_fn_js<decltype(v)::value, decltype(pr)::value>(js, L);
+  });
 }
 
 constexpr int kResidentThreads = 512;
@@ -382,10 +378,11 @@ hsg_status plan_persistent(hsg_ctx* h) {
   HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   for (Bucket& b : h->buckets) {
     const size_t spins = static_cast<size_t>(12) * h->NT * b.N;
-    const size_t bond_bytes[3] = {0, static_cast<size_t>(h->prec == HSG_F16 ? 12 : 24), 24};
+    const size_t stored = h->prec == HSG_F16 ? 12 : h->prec == HSG_BIMODAL ? 1 : 24;
+    const size_t bond_bytes[3] = {0, stored, 24};
     int best_js = -1, best_occ = 0;
     size_t best_smem = 0;
-    for (int js = (h->prec == HSG_F16 ? 2 : 1); js >= 0; --js) {
+    for (int js = (h->prec == HSG_F32 ? 1 : 2); js >= 0; --js) {
       void* fn = persistent_kernel(h->V, h->prec, js, b.L);
       cudaFuncAttributes fa;
       HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
@@ -433,6 +430,7 @@ hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
     p.accepted = h->d_pt_acc;
     p.key = philox_key(h->seed);
     p.counters = h->d_counters;
+    p.D = h->bimodal_D;
     void* args[] = {&p};
     *h->launch_sink += 1;
     HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L), dim3(b.S_b * h->n_rep),
@@ -512,6 +510,7 @@ hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
   for (const Bucket& b : h->buckets) {
     MeasureParams p;
     p.b = view(b);
+    p.b.D = h->bimodal_D;
     p.R = h->R;
     p.n_rep = h->n_rep;
     p.NT = h->NT;
@@ -524,23 +523,14 @@ hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
     const unsigned grid = static_cast<unsigned>(b.S_b * h->NT * b.P * b.m_chunks);
     const size_t smem = 2 * sizeof(float) * b.L;
     *h->launch_sink += 2;
-    if (b.m_warp) {
-      const int n_units = b.S_b * h->NT * b.P;
-      const unsigned wgrid = static_cast<unsigned>((n_units + kMeasureThreads / 32 - 1) / (kMeasureThreads / 32));
-      if (h->V == 2) {
-        if (h->prec == HSG_F16) k_measure_warp<2, kPrecF16><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
-        else k_measure_warp<2, kPrecF32><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
-      } else {
-        if (h->prec == HSG_F16) k_measure_warp<1, kPrecF16><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
-        else k_measure_warp<1, kPrecF32><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
-      }
-    } else if (h->V == 2) {
-      if (h->prec == HSG_F16) k_measure<2, kPrecF16><<<grid, kMeasureThreads, smem, st>>>(p);
-      else k_measure<2, kPrecF32><<<grid, kMeasureThreads, smem, st>>>(p);
-    } else {
-      if (h->prec == HSG_F16) k_measure<1, kPrecF16><<<grid, kMeasureThreads, smem, st>>>(p);
-      else k_measure<1, kPrecF32><<<grid, kMeasureThreads, smem, st>>>(p);
-    }
+    const int n_units = b.S_b * h->NT * b.P;
+    const unsigned wgrid = static_cast<unsigned>((n_units + kMeasureThreads / 32 - 1) / (kMeasureThreads / 32));
+    dispatch(h->V, h->prec, [&](auto v, auto pr) {
+      constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
+      if (b.m_warp) k_measure_warp<VV, P><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+      else k_measure<VV, P><<<grid, kMeasureThreads, smem, st>>>(p);
+      return 0;
+    });
     HSG_CUDA(cudaGetLastError());
     const int units = b.S_b * h->NT;
     k_measure_finalize<<<(units + 127) / 128, 128, 0, st>>>(b.d_mpart, b.d_samples, b.S_b, h->NT, b.P, b.m_chunks,
@@ -632,8 +622,10 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   if (cfg->n_samples < 1 || !cfg->L) return fail(HSG_EINVAL, "n_samples must be >= 1 and L non-NULL");
   if (cfg->n_replicas < 1 || cfg->n_temps < 1 || !cfg->beta)
     return fail(HSG_EINVAL, "n_replicas and n_temps must be >= 1 and beta non-NULL");
-  if (cfg->coupling_prec != HSG_F32 && cfg->coupling_prec != HSG_F16)
-    return fail(HSG_EINVAL, "coupling_prec must be HSG_F32 or HSG_F16");
+  if (cfg->coupling_prec != HSG_F32 && cfg->coupling_prec != HSG_F16 && cfg->coupling_prec != HSG_BIMODAL)
+    return fail(HSG_EINVAL, "coupling_prec must be HSG_F32, HSG_F16 or HSG_BIMODAL");
+  if (cfg->coupling_prec == HSG_BIMODAL && !(cfg->bimodal_D >= 0.0 && cfg->bimodal_D < 1e30))
+    return fail(HSG_EINVAL, "bimodal_D must be finite and >= 0");
   if (cfg->layout != HSG_LAYOUT_PLAIN && cfg->layout != HSG_LAYOUT_BATCHED)
     return fail(HSG_EINVAL, "layout must be HSG_LAYOUT_PLAIN or HSG_LAYOUT_BATCHED");
   if (cfg->n_or < 0 || cfg->measure_every < 0) return fail(HSG_EINVAL, "n_or and measure_every must be >= 0");
@@ -674,6 +666,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   h->R = static_cast<int>(R);
   h->V = V;
   h->prec = cfg->coupling_prec;
+  h->bimodal_D = cfg->coupling_prec == HSG_BIMODAL ? static_cast<float>(cfg->bimodal_D) : 0.0f;
   h->layout = cfg->layout;
   h->n_or = cfg->n_or;
   h->measure_every = cfg->measure_every;
@@ -845,13 +838,32 @@ hsg_status hsg_selftest_wait_timeout(hsg_t h, long long timeout_cycles) {
   return status_check(h);
 }
 
+// Device address of the couplings of context sample `sample`.
+static char* sample_coupling_ptr(hsg_t h, int sample) {
+  const Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const size_t per_sample = 3 * static_cast<size_t>(b.N) * bond_bytes(h->prec);
+  return static_cast<char*>(b.d_J) + static_cast<size_t>(h->sample_local[sample]) * per_sample;
+}
+
+// One bimodal bond as its six FP32 entries (the kernels' decoding).
+static void decode_bimodal_host(uint8_t bits, float D, float* j) {
+  const float eps = (bits & 1u) ? -1.0f : 1.0f;
+  float d[6];
+  for (int k = 0; k < 6; ++k) d[k] = ((bits >> (k + 1)) & 1u) ? -D : D;
+  j[0] = eps + d[0];
+  j[1] = eps + d[1];
+  j[2] = eps + d[2];
+  j[3] = d[3];
+  j[4] = d[4];
+  j[5] = d[5];
+}
+
 hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
   if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
+  if (h->prec == HSG_BIMODAL) return fail(HSG_EINVAL, "bimodal contexts take hsg_set_couplings_bimodal");
   Bucket& b = h->buckets[h->sample_bucket[sample]];
-  const int sb = h->sample_local[sample];
   const size_t N = b.N;
-  const size_t per_sample = 3 * N * bond_elems(h->prec);
   std::vector<char> buf(3 * N * bond_bytes(h->prec));
   if (h->prec == HSG_F32) {
     float* out = reinterpret_cast<float*>(buf.data());
@@ -869,9 +881,41 @@ hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
       }
   }
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  char* dst = static_cast<char*>(b.d_J) + sb * per_sample * (h->prec == HSG_F16 ? 2 : 4);
-  HSG_CUDA(cudaMemcpy(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  HSG_CUDA(cudaMemcpy(sample_coupling_ptr(h, sample), buf.data(), buf.size(), cudaMemcpyHostToDevice));
   h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_set_couplings_bimodal(hsg_t h, int sample, const uint8_t* bits) {
+  if (!h || !bits) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  if (h->prec != HSG_BIMODAL) return fail(HSG_EINVAL, "the context does not store bimodal couplings");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const size_t N = b.N;
+  std::vector<uint8_t> buf(3 * N);
+  for (size_t i = 0; i < N; ++i)
+    for (int mu = 0; mu < 3; ++mu) {
+      const uint8_t v = bits[i * 3 + mu];
+      if (v & 0x80u) return fail(HSG_EINVAL, "bit 7 of a bimodal bond is set");
+      buf[mu * N + storage_site(i, b.L)] = v;
+    }
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_CUDA(cudaMemcpy(sample_coupling_ptr(h, sample), buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_couplings_bimodal(hsg_t h, int sample, uint8_t* bits_out) {
+  if (!h || !bits_out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  if (h->prec != HSG_BIMODAL) return fail(HSG_EINVAL, "the context does not store bimodal couplings");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const size_t N = b.N;
+  std::vector<uint8_t> buf(3 * N);
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_CUDA(cudaMemcpy(buf.data(), sample_coupling_ptr(h, sample), buf.size(), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i)
+    for (int mu = 0; mu < 3; ++mu) bits_out[i * 3 + mu] = buf[mu * N + storage_site(i, b.L)];
   return HSG_OK;
 }
 
@@ -879,22 +923,23 @@ hsg_status hsg_get_couplings(hsg_t h, int sample, float* J6) {
   if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   Bucket& b = h->buckets[h->sample_bucket[sample]];
-  const int sb = h->sample_local[sample];
   const size_t N = b.N;
-  const size_t per_sample = 3 * N * bond_elems(h->prec);
   std::vector<char> buf(3 * N * bond_bytes(h->prec));
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  const char* src = static_cast<const char*>(b.d_J) + sb * per_sample * (h->prec == HSG_F16 ? 2 : 4);
-  HSG_CUDA(cudaMemcpy(buf.data(), src, buf.size(), cudaMemcpyDeviceToHost));
+  HSG_CUDA(cudaMemcpy(buf.data(), sample_coupling_ptr(h, sample), buf.size(), cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < N; ++i)
-    for (int mu = 0; mu < 3; ++mu)
-      for (int e = 0; e < 6; ++e) {
-        float v;
-        const size_t d = mu * N + storage_site(i, b.L);
-        if (h->prec == HSG_F32) v = reinterpret_cast<const float*>(buf.data())[d * 6 + e];
-        else v = __half2float(reinterpret_cast<const __half*>(buf.data())[d * 8 + e]);
-        J6[(i * 3 + mu) * 6 + e] = v;
+    for (int mu = 0; mu < 3; ++mu) {
+      const size_t d = mu * N + storage_site(i, b.L);
+      float* out = J6 + (i * 3 + mu) * 6;
+      if (h->prec == HSG_BIMODAL) {
+        decode_bimodal_host(reinterpret_cast<const uint8_t*>(buf.data())[d], h->bimodal_D, out);
+        continue;
       }
+      for (int e = 0; e < 6; ++e) {
+        if (h->prec == HSG_F32) out[e] = reinterpret_cast<const float*>(buf.data())[d * 6 + e];
+        else out[e] = __half2float(reinterpret_cast<const __half*>(buf.data())[d * 8 + e]);
+      }
+    }
   return HSG_OK;
 }
 
@@ -1131,6 +1176,9 @@ static void fingerprint(const hsg_ctx* h, std::vector<int64_t>& f) {
   f.push_back(h->NT);
   f.push_back(h->V);
   f.push_back(h->prec);
+  int32_t d_bits;
+  std::memcpy(&d_bits, &h->bimodal_D, sizeof d_bits);
+  f.push_back(d_bits);
   for (int L : h->Ls) f.push_back(L);
 }
 

@@ -114,6 +114,7 @@ extern "C" hsg_status hsg_energy_noalloc(const float* spins, const float* J6, in
   p.b.N = N;
   p.b.S_b = n_samples;
   p.b.G = lattices_per_sample;
+  p.b.D = 0.0f;                           // FP32 couplings: unused
   p.colour = 1;
   p.chunks = chunks;
   p.R = lattices_per_sample;

@@ -21,7 +21,9 @@
 namespace hsg {
 
 enum : int { kHB = 0, kOR = 1, kEnergyOnly = 2 };
-enum : int { kPrecF32 = 0, kPrecF16 = 1 };
+// Coupling storage: FP32 (6 floats), FP16 (6 halves + 2 pads, one 16-B
+// load) or bimodal (one byte: the signs of J = +-1 and of the six D = +-D).
+enum : int { kPrecF32 = 0, kPrecF16 = 1, kPrecBimodal = 2 };
 constexpr int kSweepThreads = 256;
 constexpr int kMeasureThreads = 256;
 constexpr int kNQ = 30;  // raw measurement sums per pair, see k_measure
@@ -31,6 +33,7 @@ struct BucketView {
   const void* J;
   const int* sample_ids;  // [S_b] global sample index
   int L, N, S_b, G;
+  float D;                // bimodal couplings: magnitude of the anisotropy
 };
 
 struct SweepParams {
@@ -48,9 +51,39 @@ struct SweepParams {
 // ---------------------------------------------------------------------------
 // Loads
 // ---------------------------------------------------------------------------
+// One bimodal bond (Sec. II.A): bit 0 is the sign of the isotropic coupling
+// J = +-1, bits 1..6 the signs of D^xx, D^yy, D^zz, D^xy, D^xz, D^yz = +-D
+// (a set bit means negative); the six stored entries of J I + D follow.
+__device__ __forceinline__ void decode_bimodal(uint32_t bits, float D, float (&j)[6]) {
+  const float eps = __int_as_float(0x3f800000 | ((bits & 1u) << 31));
+  const uint32_t d = __float_as_uint(D);
+  float dd[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) dd[k] = __uint_as_float(d ^ (((bits >> (k + 1)) & 1u) << 31));
+  j[0] = eps + dd[0];
+  j[1] = eps + dd[1];
+  j[2] = eps + dd[2];
+  j[3] = dd[3];
+  j[4] = dd[4];
+  j[5] = dd[5];
+}
+
+// The couplings of bucket sample sb (3 N bonds), in the storage format.
 template <int PREC>
-__device__ __forceinline__ void load_bond(const void* J, size_t bond, float (&j)[6]) {
-  if constexpr (PREC == kPrecF32) {
+__device__ __forceinline__ const void* sample_bonds(const void* J, int sb, int N) {
+  const size_t off = static_cast<size_t>(sb) * 3 * N;
+  if constexpr (PREC == kPrecF32) return static_cast<const float*>(J) + off * 6;
+  else if constexpr (PREC == kPrecF16) return static_cast<const uint4*>(J) + off;
+  else return static_cast<const uint8_t*>(J) + off;
+}
+
+// Bond number `bond` of J as six FP32 entries (xx, yy, zz, xy, xz, yz).  D is
+// used by the bimodal format only.
+template <int PREC>
+__device__ __forceinline__ void load_bond(const void* J, size_t bond, float (&j)[6], float D) {
+  if constexpr (PREC == kPrecBimodal) {
+    decode_bimodal(__ldg(static_cast<const uint8_t*>(J) + bond), D, j);
+  } else if constexpr (PREC == kPrecF32) {
     const float2* p = reinterpret_cast<const float2*>(static_cast<const float*>(J) + bond * 6);
     const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
     j[0] = a.x; j[1] = a.y; j[2] = b.x; j[3] = b.y; j[4] = c.x; j[5] = c.y;
@@ -306,12 +339,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
     zero3<V>(hb);
     float j[6];
     float s[3][V];
-    load_bond<PREC>(b.J, jb + i, j);              load_spin<V>(base, plane, ixp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(b.J, jb + N + i, j);          load_spin<V>(base, plane, iyp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(b.J, jb + 2 * size_t(N) + i, j);   load_spin<V>(base, plane, izp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(b.J, jb + ixm, j);            load_spin<V>(base, plane, ixm, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(b.J, jb + N + iym, j);        load_spin<V>(base, plane, iym, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(b.J, jb + 2 * size_t(N) + izm, j); load_spin<V>(base, plane, izm, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(b.J, jb + i, j, b.D);              load_spin<V>(base, plane, ixp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(b.J, jb + N + i, j, b.D);          load_spin<V>(base, plane, iyp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(b.J, jb + 2 * size_t(N) + i, j, b.D);   load_spin<V>(base, plane, izp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(b.J, jb + ixm, j, b.D);            load_spin<V>(base, plane, ixm, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(b.J, jb + N + iym, j, b.D);        load_spin<V>(base, plane, iym, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(b.J, jb + 2 * size_t(N) + izm, j, b.D); load_spin<V>(base, plane, izm, s); add_bond<V>(j, s, hb);
     combine_field<V>(hf, hb, h);
 
     if constexpr (KIND == kHB) {
@@ -451,9 +484,9 @@ __device__ __forceinline__ void add_bond1(const float (&j)[6], const float (&s)[
 // The raw sums of one site i of the replica pair (base_a, base_b), added to
 // part[kNQ].
 template <int V, int PREC>
-__device__ __forceinline__ void measure_site(const void* J, size_t jb, const float* sh_phase, const float* base_a,
-                                             const float* base_b, size_t plane, int L, int N, int i, bool do_sd,
-                                             float T, float (&part)[kNQ]) {
+__device__ __forceinline__ void measure_site(const void* J, float D, size_t jb, const float* sh_phase,
+                                             const float* base_a, const float* base_b, size_t plane, int L, int N,
+                                             int i, bool do_sd, float T, float (&part)[kNQ]) {
   const int row = i / L, jr = i - row * L;
   const int half = L >> 1;
   const int x = (jr < half) ? 2 * jr : 2 * (jr - half) + 1;
@@ -479,10 +512,10 @@ __device__ __forceinline__ void measure_site(const void* J, size_t jb, const flo
     zb[mu] = triple(ub, sbv, db);
     if (do_sd) {
       float j[6];
-      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + i, j);
+      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + i, j, D);
       add_bond1(j, ua, ha);
       add_bond1(j, ub, hb);
-      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + nb[2 * mu + 1], j);
+      load_bond<PREC>(J, jb + static_cast<size_t>(mu) * N + nb[2 * mu + 1], j, D);
       add_bond1(j, da, ha);
       add_bond1(j, db, hb);
     }
@@ -575,7 +608,7 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
   const int end = min(N, start + per_chunk);
   int batch = 0;
   for (int i = start + threadIdx.x; i < end; i += blockDim.x) {
-    measure_site<V, PREC>(b.J, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
+    measure_site<V, PREC>(b.J, b.D, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
     if (++batch == 8) {
 #pragma unroll
       for (int qq = 0; qq < kNQ; ++qq) {
@@ -626,7 +659,7 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure_warp(MeasureParams 
   for (int q = 0; q < kNQ; ++q) part[q] = 0.0f;
   int batch = 0;
   for (int i = lane; i < N; i += 32) {
-    measure_site<V, PREC>(b.J, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
+    measure_site<V, PREC>(b.J, b.D, m.jb, sh_phase, m.base_a, m.base_b, plane, L, N, i, m.do_sd, m.T, part);
     if (++batch == 8) {
 #pragma unroll
       for (int qq = 0; qq < kNQ; ++qq) {

@@ -17,9 +17,9 @@
 //   spins  [G_set][3][2 colours][N/2][V] floats
 //   bonds  [3 directions][2 colours][N/2] x 6 entries, the bond (x, x+mu)
 //          stored at its lower site x, when they fit beside the spins:
-//          JS = 1 in the stored precision (FP16: 12 B, FP32: 24 B), JS = 2
-//          converted to FP32 once at the start (24 B); JS = 0: read from
-//          global memory.
+//          JS = 1 in the stored format (FP16: 12 B, FP32: 24 B, bimodal:
+//          1 B), JS = 2 converted to FP32 once at the start (24 B); JS = 0:
+//          read from global memory.
 //
 // Work split.  The warps are divided among the lattice groups of the set
 // (wpg warps per group, or one warp looping over several groups when there
@@ -59,6 +59,7 @@ struct PersistentParams {
   long long* accepted;     // [S][n_rep][max(NT-1,1)]
   uint2 key;
   const uint32_t* counters;  // [0] heat-bath sweeps, [1] PT sweeps (at launch)
+  float D;                 // bimodal couplings: magnitude of the anisotropy
 };
 
 
@@ -91,8 +92,10 @@ __device__ __forceinline__ void sts_plane(float* base, int plane, int i, const f
 // One bond from the resident layout: the same floats as load_bond() gives for
 // the same stored entries.
 template <int PREC>
-__device__ __forceinline__ void lds_bond(const void* Js, int idx, float (&j)[6]) {
-  if constexpr (PREC == kPrecF16) {
+__device__ __forceinline__ void lds_bond(const void* Js, int idx, float (&j)[6], float D) {
+  if constexpr (PREC == kPrecBimodal) {
+    decode_bimodal(static_cast<const uint8_t*>(Js)[idx], D, j);
+  } else if constexpr (PREC == kPrecF16) {
     const uint32_t* p = static_cast<const uint32_t*>(Js) + 3 * idx;
     __half2 h0, h1, h2;
     *reinterpret_cast<uint32_t*>(&h0) = p[0];
@@ -152,8 +155,8 @@ __device__ __forceinline__ ResidentSite resident_site(int ic, int colour, const 
 // order.  sg: the group's spins, colour-split.  Js / Jg: resident or global
 // bonds.
 template <int V, int PREC, int JS>
-__device__ __forceinline__ void resident_field(const float* sg, const void* Js, const void* Jg, const int N,
-                                               int colour, int ic, const ResidentSite& r,
+__device__ __forceinline__ void resident_field(const float* sg, const void* Js, const void* Jg, float D,
+                                               const int N, int colour, int ic, const ResidentSite& r,
                                                float (&h)[3][V]) {
   constexpr int BP = JS == 2 ? kPrecF32 : PREC;        // precision of the resident bonds
   const int hN = N >> 1;
@@ -164,20 +167,20 @@ __device__ __forceinline__ void resident_field(const float* sg, const void* Js, 
   zero3<V>(hf);
   zero3<V>(hb);
   if constexpr (JS != 0) {
-    lds_bond<BP>(Js, c_own + ic, j);           lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
-    lds_bond<BP>(Js, N + c_own + ic, j);       lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
-    lds_bond<BP>(Js, 2 * N + c_own + ic, j);   lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
-    lds_bond<BP>(Js, c_nb + r.jxm, j);         lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
-    lds_bond<BP>(Js, N + c_nb + r.jym, j);     lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
-    lds_bond<BP>(Js, 2 * N + c_nb + r.jzm, j); lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
+    lds_bond<BP>(Js, c_own + ic, j, D);           lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, N + c_own + ic, j, D);       lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, 2 * N + c_own + ic, j, D);   lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
+    lds_bond<BP>(Js, c_nb + r.jxm, j, D);         lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
+    lds_bond<BP>(Js, N + c_nb + r.jym, j, D);     lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
+    lds_bond<BP>(Js, 2 * N + c_nb + r.jzm, j, D); lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
   } else {
     const size_t n = static_cast<size_t>(N);
-    load_bond<PREC>(Jg, r.gi, j);                lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jg, n + r.gi, j);            lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jg, 2 * n + r.gi, j);        lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
-    load_bond<PREC>(Jg, r.gxm, j);               lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(Jg, n + r.gym, j);           lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
-    load_bond<PREC>(Jg, 2 * n + r.gzm, j);       lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(Jg, r.gi, j, D);                lds_plane<V>(so, plane, r.jxp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, n + r.gi, j, D);            lds_plane<V>(so, plane, r.jyp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, 2 * n + r.gi, j, D);        lds_plane<V>(so, plane, r.jzp, s); add_bond<V>(j, s, hf);
+    load_bond<PREC>(Jg, r.gxm, j, D);               lds_plane<V>(so, plane, r.jxm, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(Jg, n + r.gym, j, D);           lds_plane<V>(so, plane, r.jym, s); add_bond<V>(j, s, hb);
+    load_bond<PREC>(Jg, 2 * n + r.gzm, j, D);       lds_plane<V>(so, plane, r.jzm, s); add_bond<V>(j, s, hb);
   }
   combine_field<V>(hf, hb, h);
 }
@@ -205,7 +208,8 @@ __device__ __forceinline__ ResidentWarps resident_warps(int G_set) {
 // also sums -s.h over its sites of each group it updates (FP32 terms in
 // FP64) into s_part[(g * wpg + sub) * V + v].
 template <int KIND, bool ENERGY, int V, int PREC, int JS, int LT>
-__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, const int Lrt,
+__device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, float D,
+                                                    const int Lrt,
                                                     const ResidentWarps& rw, int G_set, int colour,
                                                     const float* beta_lat, uint32_t lat_base, uint32_t t,
                                                     uint2 key, double* s_part) {
@@ -224,7 +228,7 @@ __device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, c
     for (int ic = rw.sub * 32 + lane; ic < hN; ic += rw.wpg * 32) {
       const ResidentSite r = resident_site<JS == 0>(ic, colour, L);
       float h[3][V];
-      resident_field<V, PREC, JS>(sg, Js, Jg, N, colour, ic, r, h);
+      resident_field<V, PREC, JS>(sg, Js, Jg, D, N, colour, ic, r, h);
       float o[3][V];
       if constexpr (KIND == kHB) {
         const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
@@ -289,9 +293,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(Persistent
   const int N = L * L * L;
   const int G_set = NT / V;                               // groups of this replica set
   float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * G_set) * 3 * N * V;
-  const void* Jg = (PREC == kPrecF16)
-                       ? static_cast<const void*>(static_cast<const uint4*>(p.J) + static_cast<size_t>(sb) * 3 * N)
-                       : static_cast<const void*>(static_cast<const float*>(p.J) + static_cast<size_t>(sb) * 3 * N * 6);
+  const void* Jg = sample_bonds<PREC>(p.J, sb, N);
   void* Js = sp + static_cast<size_t>(NT) * 3 * N;        // after the spins (16-byte aligned)
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(r * NT);
   const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
@@ -315,11 +317,13 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(Persistent
       const int o = d * N + colour_split_index(i, L, N);
       if constexpr (JS == 2) {
         float j[6];
-        load_bond<PREC>(Jg, q, j);
+        load_bond<PREC>(Jg, q, j, p.D);
         float2* d2 = reinterpret_cast<float2*>(static_cast<float*>(Js) + 6 * o);
         d2[0] = make_float2(j[0], j[1]);
         d2[1] = make_float2(j[2], j[3]);
         d2[2] = make_float2(j[4], j[5]);
+      } else if constexpr (PREC == kPrecBimodal) {
+        static_cast<uint8_t*>(Js)[o] = static_cast<const uint8_t*>(Jg)[q];
       } else if constexpr (PREC == kPrecF16) {
         const uint4 u = static_cast<const uint4*>(Jg)[q];
         uint32_t* w = static_cast<uint32_t*>(Js) + 3 * o;
@@ -346,26 +350,26 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(Persistent
 
   for (int step = 0; step < p.steps; ++step) {
     const uint32_t t = t_hb0 + static_cast<uint32_t>(step);
-    resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 0, s_beta_lat, lat_base, t,
+    resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base, t,
                                                      p.key, s_part);
     __syncthreads();
     if (p.n_or == 0) {
-      resident_half_sweep<kHB, true, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+      resident_half_sweep<kHB, true, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
                                                       p.key, s_part);
     } else {
-      resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+      resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
                                                        p.key, s_part);
       __syncthreads();
       for (int o = 0; o < p.n_or; ++o) {
-        resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 0, s_beta_lat, lat_base,
+        resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base,
                                                          t, p.key, s_part);
         __syncthreads();
         if (o + 1 < p.n_or) {
-          resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base,
+          resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
                                                            t, p.key, s_part);
           __syncthreads();
         } else {
-          resident_half_sweep<kOR, true, V, PREC, JS, LT>(sp, Js, Jg, L, rw, G_set, 1, s_beta_lat, lat_base,
+          resident_half_sweep<kOR, true, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
                                                           t, p.key, s_part);
         }
       }

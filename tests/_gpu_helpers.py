@@ -55,16 +55,18 @@ def colours(L):
     return (i % L + (i // L) % L + i // (L * L)) % 2
 
 
-def compare_sweep(lat, J, before, after, kind, hb_t):
+def compare_sweep(lat, J, before, after, kind, hb_t, J9s=None):
     """Per-half-sweep parity of one GPU sweep: the black half against the
     oracle's black half from `before`; the white half against the oracle's
-    white half applied to the GPU's new black spins.  Returns
-    (max |ds| over all compared components, number of frame-ambiguous sites,
-    max |du| over those sites)."""
+    white half applied to the GPU's new black spins.  J: couplings per sample
+    as given to the library, or J9s: the oracle's own bond matrices per
+    sample (bimodal couplings).  Returns (max |ds| over all compared
+    components, number of frame-ambiguous sites, max |du| over those
+    sites)."""
     tmp = temp_of(lat)
     worst, n_amb, worst_u = 0.0, 0, 0.0
     for s, L in enumerate(lat.Ls):
-        J9 = oracle.j9_from_j6(J[s])
+        J9 = J9s[s] if J9s is not None else oracle.j9_from_j6(J[s])
         col = colours(L)
         for slot in range(lat.R):
             beta = float(lat.beta[tmp[s, slot]])

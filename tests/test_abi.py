@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 25
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.hsg_version() == 1
+    assert lib.hsg_version() == hsg.ABI_VERSION == 2
 
 
 def _cfg(**kw):
@@ -53,6 +53,7 @@ def _cfg(**kw):
     c.sweep_kernel = kw.pop("sweep_kernel", 0)
     c.band_rows = kw.pop("band_rows", 0)
     c.persistent = kw.pop("persistent", 0)
+    c.bimodal_D = kw.pop("bimodal_D", 1.0)
     return c, (L, beta)
 
 
@@ -67,6 +68,8 @@ def _cfg(**kw):
     (dict(band_rows=8, sweep_kernel=1), "band_rows"),
     (dict(L=32, persistent=1), "shared memory"),
     (dict(persistent=1, layout=1, beta=[1.0, 2.0, 3.0], n_replicas=2), "multiple"),
+    (dict(prec=2, bimodal_D=-0.5), "bimodal_D"),
+    (dict(prec=2, bimodal_D=float("nan")), "bimodal_D"),
 ])
 def test_invalid_configs_rejected_on_host(lib, kw, msg):
     c, keep = _cfg(**kw)
@@ -82,6 +85,8 @@ def test_null_arguments_rejected(lib):
     assert lib.hsg_sweep_hb(None, 1) == 1
     assert lib.hsg_run_steps(None, 1) == 1
     assert lib.hsg_philox4x32_10(None, -1, None) == 1
+    assert lib.hsg_set_couplings_bimodal(None, 0, None) == 1
+    assert lib.hsg_get_couplings_bimodal(None, 0, None) == 1
     lib.hsg_destroy(None)
 
 

@@ -1,0 +1,46 @@
+"""Host-side logic of bench.py (no GPU): workload tables, the algorithmic
+byte and flop counts the roofline uses, and the synthetic inputs."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_workload_sizes():
+    for name, w in bench.WORKLOADS.items():
+        Ls = bench.sample_Ls(w)
+        assert len(Ls) == w["S"], name
+        assert all(L % 2 == 0 and L >= 4 for L in Ls), name
+    c3 = bench.sample_Ls(bench.WORKLOADS["L8x256_L12x256_R32_f16"])
+    assert c3.count(8) == 256 and c3.count(12) == 256
+    assert bench.WORKLOADS[bench.DEFAULT_WORKLOAD]["L"] == 64
+
+
+def test_algorithmic_bytes_and_flops():
+    # spins read + written (24 B) plus 3 bonds shared by R_share lattices
+    assert bench.b_alg(64, 12) == pytest.approx(24.5625)
+    assert bench.b_alg(48, 12) == pytest.approx(24.75)
+    assert bench.b_alg(1, 24) == pytest.approx(96.0)
+    assert bench.flops_per_update(8) == pytest.approx((148 + 8 * 128) / 9)
+    assert bench.flops_per_update(0) == pytest.approx(148)
+    assert bench.ALU_PEAK_TFLOPS == pytest.approx(148 * 128 * 2 * 2.032e-3)
+
+
+def test_make_inputs_small_mixed_workload():
+    w = dict(Ls=(4, 6), S=2, n_rep=2, NT=3, Tmin=0.2, Tmax=0.8, n_or=1, measure_every=1)
+    samples, J, spins, beta = bench.make_inputs(w, rank=1)
+    assert samples == [2, 3]                      # rank 1 takes the next samples
+    assert J[0].shape == (4 ** 3, 3, 6) and J[1].shape == (6 ** 3, 3, 6)
+    assert len(spins[1]) == 6 and spins[1][0].shape == (6 ** 3, 3)
+    assert np.allclose(np.linalg.norm(spins[0][0], axis=1), 1, atol=1e-6)
+    assert np.all(np.diff(beta) > 0)
+
+
+def test_traffic_keys_name_known_kernels():
+    for (h, name), v in bench.NCU_TRAFFIC.items():
+        assert len(h) == 16 and v > 0 and "k_sweep_fused" in name

@@ -56,6 +56,14 @@ MUTATIONS = {
     "sweep_colours": ("  oracle_half_sweep(L, J9, s, 1, kind, beta, seed, lattice, t);\n}",
                       "  oracle_half_sweep(L, J9, s, 0, kind, beta, seed, lattice, t);\n}",
                       ["test_oracle_updates.py"]),
+    # bimodal couplings: D^xz and D^yz bits exchanged
+    "bimodal_bit_order": ("M[0] = iso + d[0]; M[1] = d[3];       M[2] = d[4];",
+                          "M[0] = iso + d[0]; M[1] = d[3];       M[2] = d[5];",
+                          ["test_oracle_bimodal.py"]),
+    # bimodal couplings: the isotropic sign also added off the diagonal
+    "bimodal_iso_offdiag": ("M[3] = d[3];       M[4] = iso + d[1]; M[5] = d[5];",
+                            "M[3] = iso + d[3]; M[4] = iso + d[1]; M[5] = d[5];",
+                            ["test_oracle_bimodal.py"]),
     # field: one component with the wrong sign on white sites only
     "white_field_sign": ("    if (site_colour(L, i) != colour) continue;\n    double h[3], s_new[3];\n    oracle_local_field(L, J9, s, i, h);",
                       "    if (site_colour(L, i) != colour) continue;\n    double h[3], s_new[3];\n    oracle_local_field(L, J9, s, i, h);\n    if (colour == 1) { h[0] = -h[0]; }",
