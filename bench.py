@@ -1,9 +1,10 @@
 #!/usr/bin/env python
 """Throughput of the Heisenberg spin-glass Monte Carlo on one B300 (or N, as
 independent replicas): spin updates/ns of the batched FP16-coupling form,
-with the plain FP32 form, the HBM roofline fraction of the dominant kernel,
-an end-to-end figure through the public API from host buffers, and the FP64
-oracle on the host cores as a CPU baseline.
+with the plain FP32 form, the bimodal one-byte-coupling forms (plain and
+batched), the HBM roofline fraction of the dominant kernel, an end-to-end
+figure through the public API from host buffers, and the FP64 oracle on the
+host cores as a CPU baseline.
 
 Workload (default): L = 64, 8 disorder samples per GPU, 32 temperatures evenly
 spaced in [0.15, 0.75] x 2 replicas (64 lattices per sample, 512 per GPU),
@@ -210,13 +211,22 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # the hsg arm
 # ----------------------------------------------------------------------------
+# Magnitude of the anisotropy of the bimodal forms (the paper uses 0.5 and 1).
+BIMODAL_D = 1.0
+
+
 def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0,
                   persistent=False):
-    lat = hsg.Lattice(sample_Ls(w), beta, n_replicas=w["n_rep"], coupling_prec=prec,
+    import hsg_inputs as gi
+    Ls = sample_Ls(w)
+    lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=prec,
                       layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed,
-                      band_rows=band_rows, persistent=persistent)
+                      band_rows=band_rows, persistent=persistent, bimodal_D=BIMODAL_D)
     for s in range(len(samples)):
-        lat.set_couplings(s, J[s])
+        if prec == hsg.BIMODAL:
+            lat.set_couplings_bimodal(s, gi.bimodal_bits(Ls[s], seed, samples[s]))
+        else:
+            lat.set_couplings(s, J[s])
         for j in range(lat.R):
             lat.set_spins(s, j, spins[s][j])
     return lat
@@ -320,7 +330,7 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
         return dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
                     roofline=roof, lat=None)
     or_ms = time_or_kernel(lat, torch)
-    bond_bytes = 12 if prec == hsg.F16 else 24
+    bond_bytes = {hsg.F16: 12, hsg.F32: 24, hsg.BIMODAL: 1}[prec]
     r_share = R if layout == hsg.BATCHED else 1
     balg = b_alg(r_share, bond_bytes)
     plan = lat.get_sweep_plan(0)
@@ -329,7 +339,7 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
     bytes_launch = upd_launch * balg
     achieved = bytes_launch / (or_ms * 1e-3) / 1e9
     vname = 2 if layout == hsg.BATCHED else 1
-    pname = "f16" if prec == hsg.F16 else "f32"
+    pname = {hsg.F16: "f16", hsg.F32: "f32", hsg.BIMODAL: "bimodal"}[prec]
     kname = (f"k_sweep_fused<OR,{vname},{pname}> (bands of {plan['band_rows']} rows)" if plan["fused"]
              else f"k_sweep_half<OR,{vname},{pname}>")
     roof = {"bound": "hbm", "kernel": kname,
@@ -454,6 +464,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
+    ap.add_argument("--no-bimodal", action="store_true", help="skip the bimodal-coupling forms")
     ap.add_argument("--band-rows", type=int, default=0,
                     help="rows per CTA band of the fused sweep (0: library choice)")
     args = ap.parse_args()
@@ -486,6 +497,14 @@ def main():
         plain = run_form(hsg, torch, dist, w, inputs, hsg.F32, hsg.PLAIN, args.steps,
                          args.warmup, None, peak)
         plain["lat"].destroy()
+    bimodal = {}
+    if not args.no_bimodal and not persistent:
+        for key, layout in (("bimodal_plain", hsg.PLAIN), ("bimodal_batched", hsg.BATCHED)):
+            r = run_form(hsg, torch, dist, w, inputs, hsg.BIMODAL, layout, args.steps, args.warmup,
+                         None, peak)
+            r["lat"].destroy()
+            bimodal[key] = {"value": round(r["value"], 3), "ms_per_step": round(r["ms_per_step"], 3),
+                            "D": BIMODAL_D, "roofline": r["roofline"], "gpu_launches": r["launches"]}
     e2e = None if args.no_e2e else e2e_run(hsg, torch, dist, w, inputs, args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -514,6 +533,7 @@ def main():
                                   "ms_per_step": round(plain["ms_per_step"], 3),
                                   "roofline": plain["roofline"], "gpu_launches": plain["launches"]}
             line["batched_over_plain"] = round(batched["value"] / plain["value"], 3)
+        line.update(bimodal)
         if streaming is not None:
             line["streaming_f16"] = {"value": round(streaming["value"], 3),
                                      "ms_per_step": round(streaming["ms_per_step"], 3),
