@@ -13,6 +13,9 @@ Every function follows the paper (Baity-Jesi et al., arXiv:1309.1599):
   * overlaps and chiralities, Sec. II.B       -> overlap_fourier, measure_pair
   * Schwinger-Dyson identity, App. A.4.3      -> sd_residual
   * one Monte Carlo step, Sec. III / App. A.1 -> Sample.run
+  * bimodal couplings, Sec. II.A              -> bimodal_j9
+  * host analysis (xi, jackknife, log bins, crossings), Secs. II.B, III, V
+                                              -> oracle.analysis (pure Python)
 
 Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
   philox4x32   Philox round structure pinned bit for bit through the
@@ -25,6 +28,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                equivariance under global rotations and local gauge
                transformations (pins J versus J^T).
   local_field  equals minus the numerical gradient of ``energy``.
+  bimodal_j9   single-bit cases, the paper's moments over all 128 bytes,
+               time reversal, the isotropic limit (test_oracle_bimodal.py).
   energy       beta = 0 moments; high-temperature series to O(beta^3);
                ferromagnetic ground state.
   pt_sweep     exact acceptance rule checked against hand-made cases and
