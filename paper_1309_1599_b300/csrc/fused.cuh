@@ -190,31 +190,37 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
   }
 }
 
-template <int KIND, int V, int PREC>
+// LT, BT: the lattice size and band height as compile-time constants (the
+// common tilings), or 0 to take them from p at run time.  With constants the
+// ring-slot strides and plane parities fold into immediate offsets once the
+// march over z is unrolled by the ring period.
+template <int KIND, int V, int PREC, int LT = 0, int BT = 0>
 __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[kFusedSlots + 1];  // [kFusedSlots]: never completed
   __shared__ double s_red[V][kFusedMaxThreads / 32];
   __shared__ int s_failed;
 
-  const int L = p.L, half = L >> 1, N = p.N;
-  const bool full = (p.band_rows == L);
-  const int slot_rows = full ? L : p.band_rows + 4;
+  const int L = LT > 0 ? LT : p.L, half = L >> 1, N = L * L * L;
+  const int band_rows = BT > 0 ? BT : p.band_rows;
+  const int n_bands = L / band_rows;
+  const bool full = (band_rows == L);
+  const int slot_rows = full ? L : band_rows + 4;
   const int row_f = L * V;                        // floats per staged row
   const int comp_f = slot_rows * row_f;           // floats per component in a slot
   const int slot_f = 3 * comp_f;
-  const int gi = blockIdx.x / p.n_bands;
-  const int band = blockIdx.x - gi * p.n_bands;
+  const int gi = blockIdx.x / n_bands;
+  const int band = blockIdx.x - gi * n_bands;
   const int sb = gi / p.G, g = gi - sb * p.G;
-  const int y0 = band * p.band_rows;
+  const int y0 = band * band_rows;
   const int tid = threadIdx.x;
-  const int rows_t = full ? L : p.band_rows + 2;
+  const int rows_t = full ? L : band_rows + 2;
   const bool active = tid < rows_t * half;
   const int rt = active ? tid / half : 0;
   const int k = active ? tid - rt * half : 0;
   const int r = full ? rt : rt + 1;               // row within a slot
   const int y = full ? rt : (y0 - 2 + r + L) % L; // lattice row
-  const bool owner = active && (full || (r >= 2 && r < p.band_rows + 2));
+  const bool owner = active && (full || (r >= 2 && r < band_rows + 2));
   const int r_up = full ? (r + 1 == L ? 0 : r + 1) : r + 1;
   const int r_dn = full ? (r == 0 ? L - 1 : r - 1) : r - 1;
   const int k_up = (k + 1 == half) ? 0 : k + 1;
@@ -300,6 +306,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   bool failed = __syncthreads_or(!ok) != 0;
   if (!failed) first_unwaited = 1;
 
+#pragma unroll(LT > 0 ? 4 : 1)
   for (int z = 0; !failed && z <= L + 1; ++z) {
     // A thread whose wait expires flags the CTA; everyone sees the flag after
     // this step's barrier (the step's results are then discarded).
@@ -397,7 +404,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       const int nw = (blockDim.x + 31) >> 5;
       for (int w = 0; w < nw; ++w) acc += s_red[tid][w];
       const size_t lat_local = static_cast<size_t>(sb) * p.R + g * V + tid;
-      p.e_partial[lat_local * p.n_bands + band] = acc;
+      p.e_partial[lat_local * n_bands + band] = acc;
     }
   }
 }

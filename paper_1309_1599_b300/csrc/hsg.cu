@@ -219,9 +219,20 @@ hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cud
   return HSG_OK;
 }
 
+// The fused-sweep kernel for a tiling: compile-time specialisations for the
+// common ones (L = 64 in bands of 8 rows), the run-time-geometry kernel
+// otherwise.
+using FusedKernel = void (*)(FusedParams);
+
+template <int KIND, int V, int PREC>
+FusedKernel fused_kernel(int L, int band_rows) {
+  if (L == 64 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 64, 8>;
+  return k_sweep_fused<KIND, V, PREC, 0, 0>;
+}
+
 template <int KIND, int V, int PREC>
 void fused_kernel_launch(const FusedParams& p, unsigned grid, unsigned block, size_t smem, cudaStream_t st) {
-  k_sweep_fused<KIND, V, PREC><<<grid, block, smem, st>>>(p);
+  fused_kernel<KIND, V, PREC>(p.L, p.band_rows)<<<grid, block, smem, st>>>(p);
 }
 
 // One whole sweep (both colours) of a bucket with the fused kernel; reads the
@@ -266,19 +277,25 @@ hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, boo
 
 template <int KIND, int V, int PREC>
 hsg_status allow_fused_smem(size_t bytes) {
-  HSG_CUDA(cudaFuncSetAttribute(k_sweep_fused<KIND, V, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(bytes)));
+  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>})
+    HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
   return HSG_OK;
 }
 
+// Smallest block limit over a kind's fused kernels, as the driver reports it
+// for their register use; 0 if unknown.
 template <int KIND, int V, int PREC>
 int fused_max_threads_one() {
-  cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, k_sweep_fused<KIND, V, PREC>) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  int best = 1 << 30;
+  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>}) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = std::min(best, a.maxThreadsPerBlock);
   }
-  return a.maxThreadsPerBlock;
+  return best;
 }
 
 // Largest block the fused kernels (heat-bath and overrelaxation) can launch

@@ -263,6 +263,8 @@ FUSED_CASES = [
     ([40], 1, hsg.F16, hsg.BATCHED, 0),
     ([48], 1, hsg.F32, hsg.PLAIN, 0),
     ([64], 1, hsg.F16, hsg.BATCHED, 16),
+    ([64], 1, hsg.F16, hsg.BATCHED, 8),                # compile-time L = 64, 8-row tiling
+    ([64], 1, hsg.F32, hsg.PLAIN, 8),
 ]
 
 
