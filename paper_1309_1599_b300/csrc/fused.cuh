@@ -149,12 +149,14 @@ __device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) 
 // backward bonds x-1, y-1, z-1 in two partial sums).  Jb points at the
 // sample's couplings; pos, pos_xm, pos_ym, pos_zm are the storage positions
 // of the site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds
-// are this site's -x, -y, -z bonds).
+// are this site's -x, -y, -z bonds).  jz_up / jz_dn: the +z / -z bond,
+// already loaded by the caller (or null: load it here).
 template <int V, int PREC>
 __device__ __forceinline__ void site_field(const void* Jb, float D, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
                                            const float (&xp)[3][V], const float (&xm)[3][V],
                                            const float (&yu)[3][V], const float (&yd)[3][V],
-                                           const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V]) {
+                                           const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V],
+                                           const float* jz_up = nullptr, const float* jz_dn = nullptr) {
   float hf[3][V], hb[3][V], j[6];
   zero3<V>(hf);
   zero3<V>(hb);
@@ -162,13 +164,23 @@ __device__ __forceinline__ void site_field(const void* Jb, float D, int N, int p
   add_bond<V>(j, xp, hf);
   load_bond<PREC>(Jb, N + pos, j, D);
   add_bond<V>(j, yu, hf);
-  load_bond<PREC>(Jb, 2 * N + pos, j, D);
+  if (jz_up) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) j[e] = jz_up[e];
+  } else {
+    load_bond<PREC>(Jb, 2 * N + pos, j, D);
+  }
   add_bond<V>(j, zu, hf);
   load_bond<PREC>(Jb, pos_xm, j, D);
   add_bond<V>(j, xm, hb);
   load_bond<PREC>(Jb, N + pos_ym, j, D);
   add_bond<V>(j, yd, hb);
-  load_bond<PREC>(Jb, 2 * N + pos_zm, j, D);
+  if (jz_dn) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) j[e] = jz_dn[e];
+  } else {
+    load_bond<PREC>(Jb, 2 * N + pos_zm, j, D);
+  }
   add_bond<V>(j, zd, hb);
   combine_field<V>(hf, hb, h);
 }
@@ -330,11 +342,15 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       lds_site<V>(at(z, r_dn, ab, k), yd, comp_f);
       lds_site<V>(at(z + 1, r, ab, k), zu, comp_f);
       lds_site<V>(at(z - 1, r, ab, k), zd, comp_f);
+      // the z bond between this column's sites at planes z-1 and z: the
+      // black site's -z bond and the +z bond of the white site updated below
+      float jz[6];
+      load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + pz_dn * LL + yrow + ab * half + k, jz, p.D);
       {
         const int pl = pz * LL;
         site_field<V, PREC>(Jb, p.D, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
                             pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k, xp, xm, yu, yd, zu,
-                            zd, h);
+                            zd, h, nullptr, jz);
       }
       const uint32_t i_nat = static_cast<uint32_t>(2 * k + ab + L * (y + L * pz));
       update_site<KIND, V>(h, B0, beta, i_nat, lat0, t_hb, p.key);
@@ -350,7 +366,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
         lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
         site_field<V, PREC>(Jb, p.D, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
                             plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k, xp, xm, yu, yd, B0,
-                            Bm2, h);
+                            Bm2, h, jz, nullptr);
         const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));
         update_site<KIND, V>(h, w, beta, iw_nat, lat0, t_hb, p.key);
         if (want_energy) {
