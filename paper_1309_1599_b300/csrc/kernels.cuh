@@ -177,7 +177,11 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
   // logarithm of 1 - y = (1 - r0) + r0 e^{-2 kappa}, a sum of two positive
   // terms in which 1 - r0 is exact.  For kappa > 1/2, 1 - e^{-2 kappa} >= 0.63
   // cannot cancel, so the fast exponential serves both terms; expm1 is kept
-  // for small kappa, where 1 - e^{-2 kappa} is small.
+  // for small kappa, where 1 - e^{-2 kappa} is small.  For y >= 1/2 the
+  // argument of the logarithm lies in (0, 1/2], where the fast logarithm's
+  // relative error (about 2^-21) leaves w accurate to ~5e-7 relative; for
+  // y < 1/2, log1p keeps w accurate near the pole, where sin(theta) ~
+  // sqrt(2w) would amplify an absolute error.
   float w;
   if (kappa < 1e-30f) {
     w = 2.0f * r0;
@@ -191,12 +195,13 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
       e2k = em + 1.0f;
       y = -r0 * em;
     }
-    const float lg = (y < 0.5f) ? log1pf(-y) : logf(fmaf(r0, e2k, 1.0f - r0));
+    const float lg = (y < 0.5f) ? log1pf(-y) : __logf(fmaf(r0, e2k, 1.0f - r0));
     w = __fdividef(-lg, kappa);
   }
   w = fminf(fmaxf(w, 0.0f), 2.0f);
   const float u = 1.0f - w;
-  const float st = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
+  const float w2 = fmaxf(w * (2.0f - w), 0.0f);
+  const float st = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;   // sin(theta), 2 ulp
   // azimuth phi = 2 pi r1: evaluated as phi - pi in (-pi, pi), where the
   // fast sine and cosine are accurate to 2^-21.4, then reflected
   float sp, cp;
