@@ -545,7 +545,7 @@ hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
     dispatch(h->V, h->prec, [&](auto v, auto pr) {
       constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
       if (b.m_warp) k_measure_warp<VV, P><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
-      else k_measure<VV, P><<<grid, kMeasureThreads, smem, st>>>(p);
+      else k_measure<VV, P><<<grid, kMeasureThreads, measure_block_smem(b.L), st>>>(p);
       return 0;
     });
     HSG_CUDA(cudaGetLastError());
@@ -786,6 +786,22 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   if (h->persistent) {
     const hsg_status ps = plan_persistent(h);
     if (ps != HSG_OK) return bail(ps);
+  }
+  {
+    // the block measurement kernel keeps its accumulators in shared memory
+    size_t msmem = 0;
+    for (const Bucket& b : h->buckets)
+      if (!b.m_warp) msmem = std::max(msmem, measure_block_smem(b.L));
+    if (msmem > 0) {
+      const cudaError_t e = dispatch(h->V, h->prec, [&](auto v, auto pr) {
+        return cudaFuncSetAttribute(k_measure<decltype(v)::value, decltype(pr)::value>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(msmem));
+      });
+      if (e != cudaSuccess) {
+        fail(HSG_ECUDA, std::string("measurement shared memory: ") + cudaGetErrorString(e));
+        return bail(HSG_ECUDA);
+      }
+    }
   }
   const size_t S = h->S, NT = h->NT;
   hsg_status st;

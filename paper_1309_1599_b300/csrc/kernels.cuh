@@ -585,15 +585,26 @@ __device__ __forceinline__ MeasureUnit measure_unit(const MeasureParams& p, int 
   return m;
 }
 
+// Dynamic shared memory of k_measure: the per-thread FP64 accumulators
+// [kNQ][kMeasureThreads], then the phase table [L][2].
+constexpr size_t measure_block_smem(int L) {
+  return sizeof(double) * kNQ * kMeasureThreads + 2 * sizeof(float) * static_cast<size_t>(L);
+}
+
 // One block per (unit, chunk of sites).  FP32 within batches of 8 sites,
-// FP64 across batches and threads.
+// FP64 across batches (each thread's accumulators live in shared memory, so
+// that two blocks fit per SM) and threads.
 template <int V, int PREC>
-__global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
-  extern __shared__ float sh_phase[];  // [L][2]
+__global__ void __launch_bounds__(kMeasureThreads, 2) k_measure(MeasureParams p) {
+  extern __shared__ __align__(16) double m_acc[];                 // [kNQ][kMeasureThreads]
+  float* sh_phase = reinterpret_cast<float*>(m_acc + kNQ * kMeasureThreads);  // [L][2]
   __shared__ double red[kMeasureThreads / 32][kNQ];
   const BucketView& b = p.b;
   const int L = b.L, N = b.N;
   for (int t = threadIdx.x; t < 2 * L; t += blockDim.x) sh_phase[t] = p.phase[t];
+  double* acc = m_acc + threadIdx.x;                               // stride kMeasureThreads
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) acc[q * kMeasureThreads] = 0.0;
   __syncthreads();
 
   const int unit = blockIdx.x / p.chunks;
@@ -601,9 +612,6 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
   const MeasureUnit m = measure_unit<V>(p, unit);
   const size_t plane = static_cast<size_t>(N) * V;
 
-  double acc[kNQ];
-#pragma unroll
-  for (int q = 0; q < kNQ; ++q) acc[q] = 0.0;
   float part[kNQ];
 #pragma unroll
   for (int q = 0; q < kNQ; ++q) part[q] = 0.0f;
@@ -617,19 +625,17 @@ __global__ void __launch_bounds__(kMeasureThreads) k_measure(MeasureParams p) {
     if (++batch == 8) {
 #pragma unroll
       for (int qq = 0; qq < kNQ; ++qq) {
-        acc[qq] += static_cast<double>(part[qq]);
+        acc[qq * kMeasureThreads] += static_cast<double>(part[qq]);
         part[qq] = 0.0f;
       }
       batch = 0;
     }
   }
-#pragma unroll
-  for (int qq = 0; qq < kNQ; ++qq) acc[qq] += static_cast<double>(part[qq]);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int qq = 0; qq < kNQ; ++qq) {
-    const double d = warp_sum(acc[qq]);
+    const double d = warp_sum(acc[qq * kMeasureThreads] + static_cast<double>(part[qq]));
     if (lane == 0) red[warp][qq] = d;
   }
   __syncthreads();
