@@ -220,13 +220,14 @@ hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cud
 }
 
 // The fused-sweep kernel for a tiling: compile-time specialisations for the
-// common ones (L = 64 in bands of 8 rows), the run-time-geometry kernel
-// otherwise.
+// common ones (L = 64 and L = 32 in bands of 8 rows), the run-time-geometry
+// kernel otherwise.
 using FusedKernel = void (*)(FusedParams);
 
 template <int KIND, int V, int PREC>
 FusedKernel fused_kernel(int L, int band_rows) {
   if (L == 64 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 64, 8>;
+  if (L == 32 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 32, 8>;
   return k_sweep_fused<KIND, V, PREC, 0, 0>;
 }
 
@@ -277,7 +278,8 @@ hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, boo
 
 template <int KIND, int V, int PREC>
 hsg_status allow_fused_smem(size_t bytes) {
-  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>})
+  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>,
+                         k_sweep_fused<KIND, V, PREC, 32, 8>})
     HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
   return HSG_OK;
 }
@@ -287,7 +289,8 @@ hsg_status allow_fused_smem(size_t bytes) {
 template <int KIND, int V, int PREC>
 int fused_max_threads_one() {
   int best = 1 << 30;
-  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>}) {
+  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>,
+                         k_sweep_fused<KIND, V, PREC, 32, 8>}) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
       cudaGetLastError();
@@ -317,9 +320,9 @@ hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
 }
 
 // Tiling of the fused sweep for lattice size L and V lattices per element:
-// whole planes if they fit, else the widest band of rows (a divisor of L, at
-// least 8) within the thread and shared-memory limits.  False: use the
-// two-pass half-sweep kernel.
+// whole planes for L <= 16, else the smallest band of rows (a divisor of L,
+// at least 8) within the thread and shared-memory limits, else whole planes
+// if they fit.  False: use the two-pass half-sweep kernel.
 bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t* smem) {
   const size_t max_smem = 200 * 1024;
   auto smem_for = [&](int rows) { return static_cast<size_t>(kFusedSlots) * 3 * rows * L * V * sizeof(float); };
@@ -335,21 +338,29 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
     *smem = smem_for(rows_s);
     return true;
   }
-  if (threads_for(L) <= max_threads && smem_for(L) <= max_smem) {
+  const bool planes_fit = threads_for(L) <= max_threads && smem_for(L) <= max_smem;
+  if (planes_fit && L <= 16) {  // small lattices: whole planes, no halo rows
     *band_rows = L;
     *smem = smem_for(L);
     return true;
   }
-  if ((L * V) % 4 != 0) return false;  // 16-byte rows for the bulk copies
   // the smallest band that tiles L: more, smaller CTAs per SM overlap their
-  // per-plane barriers (8-row bands ran faster than 16-row ones at L = 64)
-  for (int B = 8; B <= L / 2; ++B) {
-    if (L % B != 0) continue;
-    if (threads_for(B + 2) <= max_threads && smem_for(B + 4) <= max_smem) {
-      *band_rows = B;
-      *smem = smem_for(B + 4);
-      return true;
+  // per-plane barriers (8-row bands ran faster than 16-row ones at L = 64,
+  // and than whole planes at L = 32)
+  if ((L * V) % 4 == 0) {  // 16-byte rows for the bulk copies
+    for (int B = 8; B <= L / 2; ++B) {
+      if (L % B != 0) continue;
+      if (threads_for(B + 2) <= max_threads && smem_for(B + 4) <= max_smem) {
+        *band_rows = B;
+        *smem = smem_for(B + 4);
+        return true;
+      }
     }
+  }
+  if (planes_fit) {
+    *band_rows = L;
+    *smem = smem_for(L);
+    return true;
   }
   return false;
 }
