@@ -13,7 +13,7 @@ SOURCES = [os.path.join(CSRC, "hsg.cu"), os.path.join(CSRC, "hsg_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(ROOT, "include", "hsg.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "--split-compile", "0",
          "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 
 
