@@ -297,6 +297,29 @@ def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3):
     return e0.elapsed_time(e1) / n_calls, n_kernels
 
 
+def time_sequential_or(hsg, w, inputs, torch, n_calls=3):
+    """Sequential overrelaxation sweeps (App. A.1, sites in natural order,
+    executed by hyperplanes x+y+z) of the whole workload: updates/ns and ms
+    per sweep, CUDA events on the library's stream."""
+    samples, J, spins, beta = inputs
+    lat = build_lattice(hsg, w, samples, J, spins, beta, hsg.F16, hsg.BATCHED)
+    stream = torch.cuda.current_stream()
+    lat.sweep_or_sequential(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_calls):
+        lat.sweep_or_sequential(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n_calls
+    upd = lat.R * sum(L ** 3 for L in sample_Ls(w))
+    lat.destroy()
+    return {"value": round(upd / (ms * 1e6), 3), "unit": UNIT, "ms_per_sweep": round(ms, 4),
+            "kernel": "k_sweep_or_seq<2,f16> (hyperplanes x+y+z, one lattice pair per CTA)"}
+
+
 def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0,
              persistent=False):
     samples, J, spins, beta = inputs
@@ -487,7 +510,9 @@ def main():
     if batched["lat"] is not None:
         batched["lat"].destroy()
     streaming = None
+    sequential = None
     if persistent:
+        sequential = time_sequential_or(hsg, w, inputs, torch)
         # the same workload through the streaming kernels, for comparison
         streaming = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
                              args.warmup, None, peak)
@@ -540,6 +565,8 @@ def main():
                                      "roofline": streaming["roofline"],
                                      "gpu_launches": streaming["launches"]}
             line["resident_over_streaming"] = round(batched["value"] / streaming["value"], 3)
+        if sequential is not None:
+            line["sequential_or_sweep"] = sequential
         print(json.dumps(line), flush=True)
     dist.close()
     return 0

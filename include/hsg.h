@@ -171,6 +171,17 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float *s_out);
 hsg_status hsg_sweep_hb(hsg_t h, int n);
 hsg_status hsg_sweep_or(hsg_t h, int n);
 
+/* n sequential overrelaxation sweeps of every lattice (App. A.1): the sites
+ * are visited one at a time in the natural order i = x + L (y + L z), each
+ * reflected about the field of its neighbours' current values (earlier sites
+ * already updated), so the update travels through the lattice as a wave.
+ * Executed exactly by hyperplanes x + y + z = tau, one lattice group per CTA
+ * held in shared memory: needs 12 V L^3 <= 200 KiB for every L (L <= 20 with
+ * two lattices per element, L <= 24 with one), HSG_EINVAL otherwise (nothing
+ * done).  The stored energies become stale (recomputed on demand).  Not used
+ * by hsg_run_steps, whose sweeps are checkerboard. */
+hsg_status hsg_sweep_or_sequential(hsg_t h, int n);
+
 /* Recompute the energy E = -sum_bonds s_x^T J s_y (Eq. (1)) of every lattice
  * (FP32 terms, FP64 sums). */
 hsg_status hsg_energy(hsg_t h);

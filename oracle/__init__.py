@@ -14,6 +14,7 @@ Every function follows the paper (Baity-Jesi et al., arXiv:1309.1599):
   * Schwinger-Dyson identity, App. A.4.3      -> sd_residual
   * one Monte Carlo step, Sec. III / App. A.1 -> Sample.run
   * bimodal couplings, Sec. II.A              -> bimodal_j9
+  * sequential overrelaxation, App. A.1       -> sweep_sequential
   * host analysis (xi, jackknife, log bins, crossings), Secs. II.B, III, V
                                               -> oracle.analysis (pure Python)
 
@@ -105,6 +106,7 @@ def _load():
                                                  ctypes.c_long, vp, vp, vp]),
                 "oracle_fields": (None, [i32, vp, vp, i32, vp]),
                 "oracle_bimodal_j9": (None, [ctypes.c_long, vp, d, vp]),
+                "oracle_sweep_sequential": (None, [i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -253,6 +255,14 @@ def sweep(L: int, J9, s: np.ndarray, kind: int, beta: float = 0.0, seed: int = 0
     assert s.dtype == np.float64 and s.flags.c_contiguous
     J9 = _f64(J9)
     _load().oracle_sweep(L, _ptr(J9), _ptr(s), kind, beta, seed, lattice, t)
+
+
+def sweep_sequential(L: int, J9, s: np.ndarray) -> None:
+    """One sequential overrelaxation sweep (sites in natural order, each using
+    its neighbours' current values), in place on s (float64 [N,3])."""
+    assert s.dtype == np.float64 and s.flags.c_contiguous
+    J9 = _f64(J9)
+    _load().oracle_sweep_sequential(L, _ptr(J9), _ptr(s))
 
 
 def pt_sweep(beta, E, perm: np.ndarray, seed: int, replica_set: int, t_pt: int,

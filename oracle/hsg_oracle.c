@@ -315,6 +315,22 @@ void oracle_sweep(int L, const double *J9, double *s, int kind, double beta,
   oracle_half_sweep(L, J9, s, 1, kind, beta, seed, lattice, t);
 }
 
+/* Sequential overrelaxation sweep (App. A.1): the sites are visited one at  */
+/* a time in the natural order i = x + L (y + L z), each reflected about the  */
+/* field of its neighbours' current values -- earlier sites already updated,  */
+/* later ones not -- so the update travels through the lattice as a wave.     */
+void oracle_sweep_sequential(int L, const double *J9, double *s) {
+  long N = (long)L * L * L;
+  for (long i = 0; i < N; ++i) {
+    double h[3], s_new[3];
+    oracle_local_field(L, J9, s, i, h);
+    oracle_or_update(h, s + i * 3, s_new);
+    s[i * 3 + 0] = s_new[0];
+    s[i * 3 + 1] = s_new[1];
+    s[i * 3 + 2] = s_new[2];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Parallel tempering (App. A.1): for temperature pairs (i, i+1), taken in    */
 /* order i = 0 .. n_temps-2, propose exchanging the configurations at beta_i */

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "hsg_get_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_sweep_hb": [ctypes.c_void_p, ctypes.c_int],
     "hsg_sweep_or": [ctypes.c_void_p, ctypes.c_int],
+    "hsg_sweep_or_sequential": [ctypes.c_void_p, ctypes.c_int],
     "hsg_energy": [ctypes.c_void_p],
     "hsg_get_energies": [ctypes.c_void_p, ctypes.c_void_p],
     "hsg_set_energies": [ctypes.c_void_p, ctypes.c_void_p],
@@ -253,6 +254,9 @@ class Lattice:
 
     def sweep_or(self, n: int = 1) -> None:
         _check(self._lib.hsg_sweep_or(self._h, n))
+
+    def sweep_or_sequential(self, n: int = 1) -> None:
+        _check(self._lib.hsg_sweep_or_sequential(self._h, n))
 
     def energy(self) -> None:
         _check(self._lib.hsg_energy(self._h))

@@ -17,6 +17,7 @@
 #include "../../include/hsg.h"
 #include "fused.cuh"
 #include "persistent.cuh"
+#include "sequential.cuh"
 #include "kernels.cuh"
 
 using namespace hsg;
@@ -1038,6 +1039,42 @@ hsg_status hsg_sweep_or(hsg_t h, int n) {
   if (n == 0) return HSG_OK;
   HSG_TRY(enqueue_or_sweeps(h, n, h->stream));
   h->energy_valid = true;
+  return HSG_OK;
+}
+
+// Shared memory of the sequential sweep: one lattice group in natural order.
+static constexpr size_t kSeqMaxSmem = 200 * 1024;
+
+hsg_status hsg_sweep_or_sequential(hsg_t h, int n) {
+  if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
+  size_t smem_max = 0;
+  for (const Bucket& b : h->buckets) {
+    const size_t smem = sizeof(float) * 3 * static_cast<size_t>(b.N) * h->V;
+    if (smem > kSeqMaxSmem)
+      return fail(HSG_EINVAL, "sequential sweep: a lattice group of L = " + std::to_string(b.L) +
+                                  " does not fit in shared memory (12 V L^3 <= 200 KiB)");
+    smem_max = std::max(smem_max, smem);
+  }
+  if (n == 0) return HSG_OK;
+  HSG_CUDA((dispatch(h->V, h->prec, [&](auto v, auto pr) {
+    return cudaFuncSetAttribute(k_sweep_or_seq<decltype(v)::value, decltype(pr)::value>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max));
+  })));
+  for (const Bucket& b : h->buckets) {
+    SeqParams p;
+    p.b = view(b);
+    p.b.D = h->bimodal_D;
+    p.n_sweeps = n;
+    const size_t smem = sizeof(float) * 3 * static_cast<size_t>(b.N) * h->V;
+    const unsigned grid = static_cast<unsigned>(b.S_b * b.G);
+    *h->launch_sink += 1;
+    dispatch(h->V, h->prec, [&](auto v, auto pr) {
+      k_sweep_or_seq<decltype(v)::value, decltype(pr)::value><<<grid, kSeqThreads, smem, h->stream>>>(p);
+      return 0;
+    });
+    HSG_CUDA(cudaGetLastError());
+  }
+  h->energy_valid = false;
   return HSG_OK;
 }
 

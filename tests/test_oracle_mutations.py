@@ -56,6 +56,10 @@ MUTATIONS = {
     "sweep_colours": ("  oracle_half_sweep(L, J9, s, 1, kind, beta, seed, lattice, t);\n}",
                       "  oracle_half_sweep(L, J9, s, 0, kind, beta, seed, lattice, t);\n}",
                       ["test_oracle_updates.py"]),
+    # sequential overrelaxation: sites visited in reverse order
+    "sequential_reverse": ("  for (long i = 0; i < N; ++i) {\n    double h[3], s_new[3];\n    oracle_local_field(L, J9, s, i, h);\n    oracle_or_update(h, s + i * 3, s_new);",
+                           "  for (long i = N - 1; i >= 0; --i) {\n    double h[3], s_new[3];\n    oracle_local_field(L, J9, s, i, h);\n    oracle_or_update(h, s + i * 3, s_new);",
+                           ["test_oracle_sequential.py"]),
     # bimodal couplings: D^xz and D^yz bits exchanged
     "bimodal_bit_order": ("M[0] = iso + d[0]; M[1] = d[3];       M[2] = d[4];",
                           "M[0] = iso + d[0]; M[1] = d[3];       M[2] = d[5];",
