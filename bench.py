@@ -215,12 +215,19 @@ class ClockSampler:
 BIMODAL_D = 1.0
 
 
+def philox_key(rank: int) -> int:
+    """Random-number key of a rank's context: the contexts of different ranks
+    number their samples from 0, so distinct keys keep the replicas'
+    random streams independent."""
+    return 1 + rank
+
+
 def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0,
-                  persistent=False):
+                  persistent=False, key=1):
     import hsg_inputs as gi
     Ls = sample_Ls(w)
     lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=prec,
-                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=seed,
+                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=key,
                       band_rows=band_rows, persistent=persistent, bimodal_D=BIMODAL_D)
     for s in range(len(samples)):
         if prec == hsg.BIMODAL:
@@ -324,7 +331,7 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
              persistent=False):
     samples, J, spins, beta = inputs
     lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows,
-                        persistent=persistent)
+                        persistent=persistent, key=philox_key(dist.rank))
     R = lat.R
     n_sites = sum(L ** 3 for L in sample_Ls(w))
     for _ in range(warmup):
@@ -388,7 +395,7 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     Ls, S = sample_Ls(w), len(samples)
     lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
                       layout=hsg.BATCHED, n_or=w["n_or"], measure_every=w["measure_every"],
-                      persistent=w.get("persistent", False))
+                      persistent=w.get("persistent", False), seed=philox_key(dist.rank))
     R, n_sites = lat.R, sum(L ** 3 for L in Ls)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     J_h = [pin(j) for j in J]
