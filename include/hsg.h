@@ -163,6 +163,14 @@ hsg_status hsg_get_couplings_bimodal(hsg_t h, int sample, uint8_t *bits_out);
 hsg_status hsg_set_spins(hsg_t h, int sample, int slot, const float *s);
 hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float *s_out);
 
+/* The same with a caller-owned DEVICE buffer float32 [N][3] (natural site
+ * order) on the context's device, e.g. a torch CUDA tensor: enqueued on the
+ * configured stream without synchronising, so the buffer must stay valid
+ * (and, for the getter, unread) until the stream reaches the copy.  No host
+ * copy is involved. */
+hsg_status hsg_set_spins_device(hsg_t h, int sample, int slot, const float *d_s);
+hsg_status hsg_get_spins_device(hsg_t h, int sample, int slot, float *d_out);
+
 /* n checkerboard sweeps of every lattice (App. A.1): heat-bath draws from
  * P(s) ~ exp(beta s.h) at each lattice's current temperature; overrelaxation
  * reflects s about h, s' = 2h(h.s)/h^2 - s (unchanged where h = 0).  Each

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "hsg_set_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_couplings": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_set_couplings_bimodal": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_set_spins_device": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_spins_device": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_couplings_bimodal": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_set_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
@@ -249,6 +251,19 @@ class Lattice:
         return out
 
     # -- Monte Carlo -----------------------------------------------------
+    def set_spins_device(self, sample: int, slot: int, tensor) -> None:
+        """From a contiguous float32 CUDA tensor [N, 3] on the context's device
+        (stream-ordered, no host copy)."""
+        assert tensor.is_cuda and tensor.dtype.itemsize == 4 and tensor.is_contiguous()
+        assert tensor.numel() == self.N(sample) * 3
+        _check(self._lib.hsg_set_spins_device(self._h, sample, slot, ctypes.c_void_p(tensor.data_ptr())))
+
+    def get_spins_device(self, sample: int, slot: int, tensor) -> None:
+        """Into a contiguous float32 CUDA tensor [N, 3] (stream-ordered)."""
+        assert tensor.is_cuda and tensor.dtype.itemsize == 4 and tensor.is_contiguous()
+        assert tensor.numel() == self.N(sample) * 3
+        _check(self._lib.hsg_get_spins_device(self._h, sample, slot, ctypes.c_void_p(tensor.data_ptr())))
+
     def sweep_hb(self, n: int = 1) -> None:
         _check(self._lib.hsg_sweep_hb(self._h, n))
 

@@ -1023,6 +1023,30 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float* s_out) {
   return status_check(h);
 }
 
+hsg_status hsg_set_spins_device(hsg_t h, int sample, int slot, const float* d_s) {
+  HSG_TRY(spin_slot_args(h, sample, slot));
+  if (!d_s) return fail(HSG_EINVAL, "spins pointer is NULL");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  float* base = b.d_spins[b.cur] + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  k_scatter_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(d_s, base, b.L, h->V, slot % h->V);
+  HSG_CUDA(cudaGetLastError());
+  h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins_device(hsg_t h, int sample, int slot, float* d_out) {
+  HSG_TRY(spin_slot_args(h, sample, slot));
+  if (!d_out) return fail(HSG_EINVAL, "output pointer is NULL");
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  const float* base =
+      b.d_spins[b.cur] + (static_cast<size_t>(sb) * b.G + slot / h->V) * 3 * static_cast<size_t>(b.N) * h->V;
+  k_gather_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(base, d_out, b.L, h->V, slot % h->V);
+  HSG_CUDA(cudaGetLastError());
+  return HSG_OK;
+}
+
 hsg_status hsg_sweep_hb(hsg_t h, int n) {
   if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
   for (int s = 0; s < n; ++s) {

@@ -311,3 +311,21 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     lat.synchronize()
     d, _, _ = compare_sweep(lat, J, before, state(lat), oracle.HB, hb_t)
     assert d <= SWEEP_TOL
+
+
+def test_device_pointer_spins_roundtrip():
+    """Spins set from and read into torch CUDA tensors (no host copy) equal
+    the host-buffer path, for both layouts and a slot of each parity."""
+    import torch
+    for layout in (hsg.PLAIN, hsg.BATCHED):
+        lat, _ = make([8, 12], [1.0, 2.0], n_rep=2, prec=hsg.F16, layout=layout)
+        for s, L in enumerate([8, 12]):
+            for slot in (1, 2):
+                host = gi.random_spins(L, 9, s, slot)
+                dev = torch.from_numpy(host).cuda()
+                lat.set_spins_device(s, slot, dev)
+                assert np.array_equal(lat.get_spins(s, slot), host)
+                out = torch.empty_like(dev)
+                lat.get_spins_device(s, slot, out)
+                torch.cuda.synchronize()
+                assert np.array_equal(out.cpu().numpy(), host)
