@@ -111,3 +111,22 @@ def test_measurement_schwinger_dyson_terms_use_the_bimodal_field():
             # accumulated per temperature as the sum over the replicas
             sd = sum(oracle.sd_residual(L, J9s[s], st[s][perm[s, r, k]], 1.0 / beta) for r in range(2))
             assert abs(obs[s, k, 8] - sd) <= 2e-5 * max(1.0, abs(sd)), (s, k, obs[s, k, 8], sd)
+
+
+def test_checkpoint_resume_is_bit_identical_and_checks_D(tmp_path):
+    betas = gi.linear_betas(0.3, 1.0, 2)
+    a, _, _ = make_bimodal([8], betas, 0.5, layout=hsg.BATCHED, measure_every=1)
+    a.run_steps(3)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.run_steps(3)
+    b = hsg.Lattice([8], betas, n_replicas=2, coupling_prec=hsg.BIMODAL, layout=hsg.BATCHED,
+                    measure_every=1, seed=SEED, bimodal_D=0.5)
+    b.load(path)
+    b.run_steps(3)
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.get_couplings_bimodal(0), b.get_couplings_bimodal(0))
+    c = hsg.Lattice([8], betas, n_replicas=2, coupling_prec=hsg.BIMODAL, layout=hsg.BATCHED,
+                    measure_every=1, seed=SEED, bimodal_D=1.0)
+    with pytest.raises(hsg.HsgError):
+        c.load(path)                                   # another D: refused
