@@ -53,6 +53,8 @@ WORKLOADS = {
                                    Tmax=0.8, n_or=8, measure_every=10, persistent=True),
 }
 DEFAULT_WORKLOAD = "L64_S8_R64_f16"
+# the small-lattice workload summarised in every run of another workload
+SMALL_WORKLOAD = "L8x256_L12x256_R32_f16"
 
 # DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by a
 # hash of the device sources that kernel is built from (stale -> null).
@@ -495,6 +497,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
     ap.add_argument("--no-bimodal", action="store_true", help="skip the bimodal-coupling forms")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the summary of the small-lattice workload (resident steps)")
     ap.add_argument("--band-rows", type=int, default=0,
                     help="rows per CTA band of the fused sweep (0: library choice)")
     args = ap.parse_args()
@@ -537,6 +541,25 @@ def main():
             r["lat"].destroy()
             bimodal[key] = {"value": round(r["value"], 3), "ms_per_step": round(r["ms_per_step"], 3),
                             "D": BIMODAL_D, "roofline": r["roofline"], "gpu_launches": r["launches"]}
+    small = None
+    if not args.no_small and not persistent:
+        # many small lattices: resident steps against the streaming kernels,
+        # and the sequential overrelaxation sweep, on the same inputs
+        ws = WORKLOADS[SMALL_WORKLOAD]
+        inputs_s = make_inputs(ws, rank)
+        k = max(2, args.steps // 2)
+        res = run_form(hsg, torch, dist, ws, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
+                       persistent=True)
+        strm = run_form(hsg, torch, dist, ws, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak)
+        strm["lat"].destroy()
+        small = {"workload": SMALL_WORKLOAD, "steps": k,
+                 "resident": {"value": round(res["value"], 3), "ms_per_step": round(res["ms_per_step"], 3),
+                              "roofline": res["roofline"], "gpu_launches": res["launches"]},
+                 "streaming_f16": {"value": round(strm["value"], 3),
+                                   "ms_per_step": round(strm["ms_per_step"], 3)},
+                 "resident_over_streaming": round(res["value"] / strm["value"], 3),
+                 "sequential_or_sweep": time_sequential_or(hsg, ws, inputs_s, torch)}
+        del inputs_s
     e2e = None if args.no_e2e else e2e_run(hsg, torch, dist, w, inputs, args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -574,6 +597,8 @@ def main():
             line["resident_over_streaming"] = round(batched["value"] / streaming["value"], 3)
         if sequential is not None:
             line["sequential_or_sweep"] = sequential
+        if small is not None:
+            line["small_lattices"] = small
         print(json.dumps(line), flush=True)
     dist.close()
     return 0
