@@ -57,12 +57,16 @@ DEFAULT_WORKLOAD = "L64_S8_R64_f16"
 SMALL_WORKLOAD = "L8x256_L12x256_R32_f16"
 
 # DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by a
-# hash of the device sources that kernel is built from (stale -> null).
+# hash of the device sources that kernel is built from (stale -> null), the
+# workload and the kernel.
 FUSED_SOURCES = ("kernels.cuh", "fused.cuh", "philox.cuh")
 RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
     # profiles/k_sweep_fused_or_L64_S1_R64_f16.md: 391.3 MB for one sample, x8 samples
-    ("21c7c0fc81184452", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3130345472,
+    ("21c7c0fc81184452", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3130345472,
+    # profiles/k_persistent_L8x256_L12x256_R32_f16.md: both launches of 10 MCS
+    ("fb8181e036b27878", "L8x256_L12x256_R32_f16",
+     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361460480,
 }
 
 
@@ -329,8 +333,9 @@ def time_sequential_or(hsg, w, inputs, torch, n_calls=3):
             "kernel": "k_sweep_or_seq<2,f16> (hyperplanes x+y+z, one lattice pair per CTA)"}
 
 
-def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0,
+def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0,
              persistent=False):
+    w = WORKLOADS[wname]
     samples, J, spins, beta = inputs
     lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows,
                         persistent=persistent, key=philox_key(dist.rank))
@@ -359,6 +364,8 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
                 "ms_per_10_mcs": round(k_ms, 4),
                 "updates_per_ns_kernel": round(upd / (k_ms * 1e6), 2),
                 "traffic": None}
+        # DRAM bytes of both launches (one per L) of 10 MCS
+        roof["traffic"] = NCU_TRAFFIC.get((kernel_source_hash(RESIDENT_SOURCES), wname, roof["kernel"]))
         return dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
                     roofline=roof, lat=None)
     or_ms = time_or_kernel(lat, torch)
@@ -381,7 +388,7 @@ def run_form(hsg, torch, dist, w, inputs, prec, layout, steps, warmup, sampler, 
             "bytes_per_launch": int(bytes_launch), "launch_ms": round(or_ms, 4),
             "updates_per_ns_roofline": round(peak[0] / balg, 2),
             "traffic": None}
-    key = (kernel_source_hash(), roof["kernel"])
+    key = (kernel_source_hash(), wname, roof["kernel"])
     if key in NCU_TRAFFIC:
         roof["traffic"] = NCU_TRAFFIC[key]
     out = dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
@@ -516,7 +523,7 @@ def main():
 
     sampler = ClockSampler(local)
     persistent = w.get("persistent", False)
-    batched = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
+    batched = run_form(hsg, torch, dist, args.workload, inputs, hsg.F16, hsg.BATCHED, args.steps,
                        args.warmup, sampler, peak, band_rows=args.band_rows, persistent=persistent)
     if batched["lat"] is not None:
         batched["lat"].destroy()
@@ -525,18 +532,18 @@ def main():
     if persistent:
         sequential = time_sequential_or(hsg, w, inputs, torch)
         # the same workload through the streaming kernels, for comparison
-        streaming = run_form(hsg, torch, dist, w, inputs, hsg.F16, hsg.BATCHED, args.steps,
+        streaming = run_form(hsg, torch, dist, args.workload, inputs, hsg.F16, hsg.BATCHED, args.steps,
                              args.warmup, None, peak)
         streaming["lat"].destroy()
     plain = None
     if not args.no_plain and not persistent:
-        plain = run_form(hsg, torch, dist, w, inputs, hsg.F32, hsg.PLAIN, args.steps,
+        plain = run_form(hsg, torch, dist, args.workload, inputs, hsg.F32, hsg.PLAIN, args.steps,
                          args.warmup, None, peak)
         plain["lat"].destroy()
     bimodal = {}
     if not args.no_bimodal and not persistent:
         for key, layout in (("bimodal_plain", hsg.PLAIN), ("bimodal_batched", hsg.BATCHED)):
-            r = run_form(hsg, torch, dist, w, inputs, hsg.BIMODAL, layout, args.steps, args.warmup,
+            r = run_form(hsg, torch, dist, args.workload, inputs, hsg.BIMODAL, layout, args.steps, args.warmup,
                          None, peak)
             r["lat"].destroy()
             bimodal[key] = {"value": round(r["value"], 3), "ms_per_step": round(r["ms_per_step"], 3),
@@ -548,9 +555,9 @@ def main():
         ws = WORKLOADS[SMALL_WORKLOAD]
         inputs_s = make_inputs(ws, rank)
         k = max(2, args.steps // 2)
-        res = run_form(hsg, torch, dist, ws, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
+        res = run_form(hsg, torch, dist, SMALL_WORKLOAD, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
                        persistent=True)
-        strm = run_form(hsg, torch, dist, ws, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak)
+        strm = run_form(hsg, torch, dist, SMALL_WORKLOAD, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak)
         strm["lat"].destroy()
         small = {"workload": SMALL_WORKLOAD, "steps": k,
                  "resident": {"value": round(res["value"], 3), "ms_per_step": round(res["ms_per_step"], 3),

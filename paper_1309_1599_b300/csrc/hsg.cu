@@ -57,6 +57,8 @@ struct Bucket {
   int res_js = 0;             // resident steps: bonds in global memory (0), resident as
                               // stored (1) or resident as FP32 (2)
   size_t res_smem = 0;        // resident steps: dynamic shared memory per CTA
+  int res_gp = 1;             // resident steps: lattice groups per work item
+  int res_threads = 512;      // resident steps: threads per CTA
 };
 
 }  // namespace
@@ -366,13 +368,18 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
   return false;
 }
 
-// Resident-step kernel for (V, precision, bond residency, L): L = 8 and 12
-// have compile-time specialisations when the bonds are resident.
+// Resident-step kernel for (V, precision, bond residency, L, groups per
+// item): L = 8 and 12 have compile-time specialisations when the bonds are
+// resident, and with two lattices per element also two-group items (gp = 2).
 template <int V, int PREC, int JS>
-void* persistent_fn_L(int L) {
+void* persistent_fn_L(int L, int gp) {
   if constexpr (JS == 0) {
     return reinterpret_cast<void*>(k_persistent<V, PREC, 0, 0>);
   } else {
+    if constexpr (V == 2) {
+      if (gp == 2 && L == 8) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 8, 2>);
+      if (gp == 2 && L == 12) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 12, 2>);
+    }
     if (L == 8) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 8>);
     if (L == 12) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 12>);
     return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 0>);
@@ -380,22 +387,46 @@ void* persistent_fn_L(int L) {
 }
 
 template <int V, int PREC>
-void* persistent_fn_js(int js, int L) {
-  if (js == 0) return persistent_fn_L<V, PREC, 0>(L);
+void* persistent_fn_js(int js, int L, int gp) {
+  if (js == 0) return persistent_fn_L<V, PREC, 0>(L, 1);
   if constexpr (PREC == kPrecF32) {
-    return persistent_fn_L<V, PREC, 1>(L);  // FP32 bonds are resident as stored
+    return persistent_fn_L<V, PREC, 1>(L, gp);  // FP32 bonds are resident as stored
   } else {
-    return js == 1 ? persistent_fn_L<V, PREC, 1>(L) : persistent_fn_L<V, PREC, 2>(L);
+    return js == 1 ? persistent_fn_L<V, PREC, 1>(L, gp) : persistent_fn_L<V, PREC, 2>(L, gp);
   }
 }
 
-void* persistent_kernel(int V, int prec, int js, int L) {
+void* persistent_kernel(int V, int prec, int js, int L, int gp) {
   return dispatch(V, prec, [&](auto v, auto pr) {
-    return persistent_fn_js<decltype(v)::value, decltype(pr)::value>(js, L);
+    return persistent_fn_js<decltype(v)::value, decltype(pr)::value>(js, L, gp);
   });
 }
 
-constexpr int kResidentThreads = 512;
+// Lattice groups per work item of the resident kernel: two where a
+// specialisation exists and the groups of a replica set pair up.
+int persistent_gp(int V, int NT, int js, int L) {
+  return (V == 2 && js != 0 && (L == 8 || L == 12) && (NT / V) % 2 == 0) ? 2 : 1;
+}
+
+// Threads of a resident CTA: 512 for the generic kernel; for an L
+// specialisation the warp count from 16 to its limit that takes the fewest
+// rounds over `items` work items of hN sites each (warps split evenly over
+// the items in flight, 32 sites per warp and round), the smallest such.
+int persistent_threads(int items, int hN, int max_threads) {
+  if (max_threads >= kPersistentMaxThreads) return 512;
+  int best_w = 16;
+  long best = -1;
+  for (int W = 16; W <= max_threads / 32; ++W) {
+    const int wpg = W >= items ? W / items : 1;
+    const int gpp = W / wpg;
+    const long rounds = static_cast<long>((items + gpp - 1) / gpp) * ((hN + 32 * wpg - 1) / (32 * wpg));
+    if (best < 0 || rounds < best) {
+      best = rounds;
+      best_w = W;
+    }
+  }
+  return 32 * best_w;
+}
 
 // Plans the resident steps of every bucket: spins 12 N_T N bytes, plus the
 // bonds (3 N per sample) when they fit beside them -- converted to FP32
@@ -409,10 +440,11 @@ hsg_status plan_persistent(hsg_ctx* h) {
     const size_t spins = static_cast<size_t>(12) * h->NT * b.N;
     const size_t stored = h->prec == HSG_F16 ? 12 : h->prec == HSG_BIMODAL ? 1 : 24;
     const size_t bond_bytes[3] = {0, stored, 24};
-    int best_js = -1, best_occ = 0;
+    int best_js = -1, best_occ = 0, best_threads = 0;
     size_t best_smem = 0;
     for (int js = (h->prec == HSG_F32 ? 1 : 2); js >= 0; --js) {
-      void* fn = persistent_kernel(h->V, h->prec, js, b.L);
+      const int gp = persistent_gp(h->V, h->NT, js, b.L);
+      void* fn = persistent_kernel(h->V, h->prec, js, b.L, gp);
       cudaFuncAttributes fa;
       HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
       const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
@@ -420,16 +452,20 @@ hsg_status plan_persistent(hsg_ctx* h) {
       if (smem > budget) continue;
       HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(budget)));
       int occ = 0;
-      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kResidentThreads, smem));
+      const int threads = persistent_threads(h->NT / h->V / gp, b.N / 2, fa.maxThreadsPerBlock);
+      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
       if (occ > best_occ) {
         best_js = js;
         best_occ = occ;
         best_smem = smem;
+        best_threads = threads;
       }
     }
     if (best_js < 0) return fail(HSG_EINVAL, "a replica set does not fit in shared memory");
     b.res_js = best_js;
     b.res_smem = best_smem;
+    b.res_gp = persistent_gp(h->V, h->NT, best_js, b.L);
+    b.res_threads = best_threads;
   }
   return HSG_OK;
 }
@@ -462,8 +498,8 @@ hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
     p.D = h->bimodal_D;
     void* args[] = {&p};
     *h->launch_sink += 1;
-    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L), dim3(b.S_b * h->n_rep),
-                              dim3(kResidentThreads), args, b.res_smem, st));
+    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L, b.res_gp), dim3(b.S_b * h->n_rep),
+                              dim3(b.res_threads), args, b.res_smem, st));
   }
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }

@@ -21,13 +21,15 @@
 //          1 B), JS = 2 converted to FP32 once at the start (24 B); JS = 0:
 //          read from global memory.
 //
-// Work split.  The warps are divided among the lattice groups of the set
-// (wpg warps per group, or one warp looping over several groups when there
-// are more groups than warps), so each thread updates sites of one group at
-// a time; the energies (E = -sum over white sites of s.h, every bond having
-// one white end) are accumulated in the last white half-sweep of the step,
-// where the white sites' fields are computed anyway, and reduced per group
-// in a fixed order.
+// Work split.  The warps are divided among work items of GP lattice groups
+// each (wpg warps per item, or one warp looping over several items when
+// there are more items than warps).  A thread updates one site of every
+// group of its item at a time: with GP = 2 (two lattices per element and an
+// even number of groups) each bond is read and converted once for four
+// lattices, and the per-group arithmetic is unchanged.  The energies
+// (E = -sum over white sites of s.h, every bond having one white end) are
+// accumulated in the last white half-sweep of the step, where the white
+// sites' fields are computed anyway, and reduced per group in a fixed order.
 //
 // The arithmetic is that of the streaming kernels: the same field summation
 // (forward and backward partial sums), the same single-spin updates and the
@@ -43,6 +45,14 @@
 namespace hsg {
 
 constexpr int kPersistentMaxThreads = 1024;
+
+// Launch bounds of the L specialisations: L = 12 runs one CTA per SM (its
+// spins alone take 166 KB at 8 temperatures) and may use up to 102
+// registers a thread at 640 threads; L = 8 runs two CTAs of 512 threads.
+template <int LT>
+constexpr int persistent_max_threads() { return LT == 12 ? 640 : LT == 8 ? 512 : kPersistentMaxThreads; }
+template <int LT>
+constexpr int persistent_min_blocks() { return LT == 8 ? 2 : 1; }
 constexpr int kMaxTempsResident = 64;
 constexpr int kMaxStepsPerLaunch = 256;
 
@@ -185,6 +195,60 @@ __device__ __forceinline__ void resident_field(const float* sg, const void* Js, 
   combine_field<V>(hf, hb, h);
 }
 
+// resident_field for GP lattice groups at once (same site, same colour):
+// each bond is read (and converted) once and applied to every group, each
+// group's field summed in resident_field's order.  sgs[q]: group q's spins.
+template <int V, int PREC, int JS, int GP>
+__device__ __forceinline__ void resident_field_gp(float* const (&sgs)[GP], const void* Js, const void* Jg, float D,
+                                                  const int N, int colour, int ic, const ResidentSite& r,
+                                                  float (&h)[GP][3][V]) {
+  if constexpr (GP == 1) {
+    float h1[3][V];
+    resident_field<V, PREC, JS>(sgs[0], Js, Jg, D, N, colour, ic, r, h1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) h[0][c][v] = h1[c][v];
+  } else {
+    constexpr int BP = JS == 2 ? kPrecF32 : PREC;
+    const int hN = N >> 1;
+    const int plane = N * V;
+    const int off_nb = (colour ^ 1) * hN * V;            // neighbours' colour
+    const int c_own = colour * hN, c_nb = (colour ^ 1) * hN;
+    float hf[GP][3][V], hb[GP][3][V], j[6], s[3][V];
+#pragma unroll
+    for (int q = 0; q < GP; ++q) {
+      zero3<V>(hf[q]);
+      zero3<V>(hb[q]);
+    }
+    auto apply = [&](int nb, float (&acc)[GP][3][V]) {
+#pragma unroll
+      for (int q = 0; q < GP; ++q) {
+        lds_plane<V>(sgs[q] + off_nb, plane, nb, s);
+        add_bond<V>(j, s, acc[q]);
+      }
+    };
+    if constexpr (JS != 0) {
+      lds_bond<BP>(Js, c_own + ic, j, D);           apply(r.jxp, hf);
+      lds_bond<BP>(Js, N + c_own + ic, j, D);       apply(r.jyp, hf);
+      lds_bond<BP>(Js, 2 * N + c_own + ic, j, D);   apply(r.jzp, hf);
+      lds_bond<BP>(Js, c_nb + r.jxm, j, D);         apply(r.jxm, hb);
+      lds_bond<BP>(Js, N + c_nb + r.jym, j, D);     apply(r.jym, hb);
+      lds_bond<BP>(Js, 2 * N + c_nb + r.jzm, j, D); apply(r.jzm, hb);
+    } else {
+      const size_t n = static_cast<size_t>(N);
+      load_bond<PREC>(Jg, r.gi, j, D);              apply(r.jxp, hf);
+      load_bond<PREC>(Jg, n + r.gi, j, D);          apply(r.jyp, hf);
+      load_bond<PREC>(Jg, 2 * n + r.gi, j, D);      apply(r.jzp, hf);
+      load_bond<PREC>(Jg, r.gxm, j, D);             apply(r.jxm, hb);
+      load_bond<PREC>(Jg, n + r.gym, j, D);         apply(r.jym, hb);
+      load_bond<PREC>(Jg, 2 * n + r.gzm, j, D);     apply(r.jzm, hb);
+    }
+#pragma unroll
+    for (int q = 0; q < GP; ++q) combine_field<V>(hf[q], hb[q], h[q]);
+  }
+}
+
 // Warp layout of a CTA over the G_set lattice groups of its replica set.
 struct ResidentWarps {
   int wpg;    // warps per group
@@ -204,10 +268,11 @@ __device__ __forceinline__ ResidentWarps resident_warps(int G_set) {
 }
 
 // One colour half-sweep (KIND: heat-bath or overrelaxation) of the resident
-// replica set.  With ENERGY (the last white half-sweep of a step), each warp
-// also sums -s.h over its sites of each group it updates (FP32 terms in
-// FP64) into s_part[(g * wpg + sub) * V + v].
-template <int KIND, bool ENERGY, int V, int PREC, int JS, int LT>
+// replica set.  The warps take items of GP groups (groups gi*GP .. gi*GP+GP-1)
+// and, within an item, sites.  With ENERGY (the last white half-sweep of a
+// step), each warp also sums -s.h over its sites of each group it updates
+// (FP32 terms in FP64) into s_part[(g * wpg + sub) * V + v].
+template <int KIND, bool ENERGY, int V, int PREC, int JS, int LT, int GP>
 __device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, const void* Jg, float D,
                                                     const int Lrt,
                                                     const ResidentWarps& rw, int G_set, int colour,
@@ -218,45 +283,57 @@ __device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, c
   const int hN = N >> 1;
   const int plane = N * V;
   const int lane = threadIdx.x & 31;
+  const int G_items = G_set / GP;
   if (rw.g0 >= rw.gpp) return;
-  for (int g = rw.g0; g < G_set; g += rw.gpp) {
-    float* sg = sp + g * 3 * plane;
-    float* own = sg + colour * hN * V;
-    double acc[V];
+  for (int gi = rw.g0; gi < G_items; gi += rw.gpp) {
+    float* sgs[GP];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+    for (int q = 0; q < GP; ++q) sgs[q] = sp + (gi * GP + q) * 3 * plane;
+    double acc[GP][V];
+#pragma unroll
+    for (int q = 0; q < GP; ++q)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[q][v] = 0.0;
     for (int ic = rw.sub * 32 + lane; ic < hN; ic += rw.wpg * 32) {
       const ResidentSite r = resident_site<JS == 0>(ic, colour, L);
-      float h[3][V];
-      resident_field<V, PREC, JS>(sg, Js, Jg, D, N, colour, ic, r, h);
-      float o[3][V];
-      if constexpr (KIND == kHB) {
-        const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
-        const uint4 u =
-            philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
+      float h[GP][3][V];
+      resident_field_gp<V, PREC, JS, GP>(sgs, Js, Jg, D, N, colour, ic, r, h);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const uint32_t lat = lat0 + v;
-          heat_bath_draw(h[0][v], h[1][v], h[2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
-                         (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
+      for (int q = 0; q < GP; ++q) {
+        const int g = gi * GP + q;
+        float* own = sgs[q] + colour * hN * V;
+        float o[3][V];
+        if constexpr (KIND == kHB) {
+          const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
+          const uint4 u =
+              philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const uint32_t lat = lat0 + v;
+            heat_bath_draw(h[q][0][v], h[q][1][v], h[q][2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
+                           (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
+          }
+        } else {
+          lds_plane<V>(own, plane, ic, o);
+          overrelax_v<V>(h[q], o);
         }
-      } else {
-        lds_plane<V>(own, plane, ic, o);
-        overrelax_v<V>(h, o);
-      }
-      sts_plane<V>(own, plane, ic, o);
-      if constexpr (ENERGY) {
+        sts_plane<V>(own, plane, ic, o);
+        if constexpr (ENERGY) {
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          acc[v] -= static_cast<double>(fmaf(o[0][v], h[0][v], fmaf(o[1][v], h[1][v], o[2][v] * h[2][v])));
+          for (int v = 0; v < V; ++v)
+            acc[q][v] -= static_cast<double>(
+                fmaf(o[0][v], h[q][0][v], fmaf(o[1][v], h[q][1][v], o[2][v] * h[q][2][v])));
+        }
       }
     }
     if constexpr (ENERGY) {
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const double d = warp_sum(acc[v]);
-        if (lane == 0) s_part[(g * rw.wpg + rw.sub) * V + v] = d;
-      }
+      for (int q = 0; q < GP; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const double d = warp_sum(acc[q][v]);
+          if (lane == 0) s_part[((gi * GP + q) * rw.wpg + rw.sub) * V + v] = d;
+        }
     }
   }
 }
@@ -276,9 +353,11 @@ __device__ __forceinline__ int colour_split_index(int i, int L, int N) {
 
 // K whole steps of every replica set of one L.  V: lattices per element;
 // PREC: stored coupling precision; JS: bond residency (see above); LT: L as
-// a compile-time constant, or 0 for the runtime p.L.
-template <int V, int PREC, int JS, int LT>
-__global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(PersistentParams p) {
+// a compile-time constant, or 0 for the runtime p.L; GP: lattice groups per
+// work item (2: each bond read and converted once for two groups).
+template <int V, int PREC, int JS, int LT, int GP = 1>
+__global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_blocks<LT>())
+    k_persistent(PersistentParams p) {
   extern __shared__ __align__(16) float sp[];
   __shared__ double s_E[kMaxTempsResident];
   __shared__ double s_part[kMaxTempsResident * 2];  // per (group, warp of the group, lattice)
@@ -298,7 +377,7 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(Persistent
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(r * NT);
   const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
-  const ResidentWarps rw = resident_warps(G_set);
+  const ResidentWarps rw = resident_warps(G_set / GP);
 
   // replica set -> shared memory, parity-split rows -> colour split; one
   // element = the V interleaved lattices of a site
@@ -350,26 +429,26 @@ __global__ void __launch_bounds__(kPersistentMaxThreads) k_persistent(Persistent
 
   for (int step = 0; step < p.steps; ++step) {
     const uint32_t t = t_hb0 + static_cast<uint32_t>(step);
-    resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base, t,
+    resident_half_sweep<kHB, false, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base, t,
                                                      p.key, s_part);
     __syncthreads();
     if (p.n_or == 0) {
-      resident_half_sweep<kHB, true, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+      resident_half_sweep<kHB, true, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
                                                       p.key, s_part);
     } else {
-      resident_half_sweep<kHB, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
+      resident_half_sweep<kHB, false, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base, t,
                                                        p.key, s_part);
       __syncthreads();
       for (int o = 0; o < p.n_or; ++o) {
-        resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base,
+        resident_half_sweep<kOR, false, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 0, s_beta_lat, lat_base,
                                                          t, p.key, s_part);
         __syncthreads();
         if (o + 1 < p.n_or) {
-          resident_half_sweep<kOR, false, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
+          resident_half_sweep<kOR, false, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
                                                            t, p.key, s_part);
           __syncthreads();
         } else {
-          resident_half_sweep<kOR, true, V, PREC, JS, LT>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
+          resident_half_sweep<kOR, true, V, PREC, JS, LT, GP>(sp, Js, Jg, p.D, L, rw, G_set, 1, s_beta_lat, lat_base,
                                                           t, p.key, s_part);
         }
       }

@@ -42,5 +42,9 @@ def test_make_inputs_small_mixed_workload():
 
 
 def test_traffic_keys_name_known_kernels():
-    for (h, name), v in bench.NCU_TRAFFIC.items():
-        assert len(h) == 16 and v > 0 and "k_sweep_fused" in name
+    for (h, wname, name), v in bench.NCU_TRAFFIC.items():
+        assert len(h) == 16 and v > 0 and wname in bench.WORKLOADS
+        assert name.startswith("k_sweep_fused") or name.startswith("k_persistent")
+    # the entries are current: each names the hash of the sources as they stand
+    hashes = {bench.kernel_source_hash(), bench.kernel_source_hash(bench.RESIDENT_SOURCES)}
+    assert {h for h, _, _ in bench.NCU_TRAFFIC} <= hashes

@@ -20,6 +20,8 @@ CASES = [
     ([12, 8], 8, 2, hsg.F32, hsg.BATCHED, 2, 2, 4),
     # heat-bath only: the energies come from the white heat-bath half-sweep
     ([8, 12], 4, 2, hsg.F16, hsg.BATCHED, 0, 2, 4),
+    # three lattice groups per replica set: one group per work item
+    ([8, 12], 6, 2, hsg.F16, hsg.BATCHED, 2, 2, 4),
 ]
 
 
