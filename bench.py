@@ -408,23 +408,20 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     R, n_sites = lat.R, sum(L ** 3 for L in Ls)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     J_h = [pin(j) for j in J]
-    s_h = [[pin(x) for x in row] for row in spins]
-    out_h = [[torch.empty((Ls[s] ** 3, 3), dtype=torch.float32).pin_memory() for _ in range(R)]
-             for s in range(S)]
+    s_h = [pin(np.stack(row)) for row in spins]            # [R][N][3] per sample
+    out_h = [torch.empty((R, Ls[s] ** 3, 3), dtype=torch.float32).pin_memory() for s in range(S)]
     lat.run_steps(1)                   # capture graphs outside the timed region
     torch.cuda.synchronize()
     dist.barrier()
     t0 = time.perf_counter()
     for s in range(S):
-        lat.set_couplings(s, J_h[s].numpy())
-        for j in range(R):
-            lat.set_spins(s, j, s_h[s][j])
+        lat.set_couplings(s, J_h[s])
+        lat.set_spins_sample(s, s_h[s])
     for _ in range(steps):
         lat.run_steps(MCS_PER_STEP)
     obs, counts = lat.read_observables()
     for s in range(S):
-        for j in range(R):
-            lat.get_spins(s, j, out=out_h[s][j])
+        lat.get_spins_sample(s, out=out_h[s])
     torch.cuda.synchronize()
     dt = dist.max(time.perf_counter() - t0)
     lat.destroy()

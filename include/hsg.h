@@ -163,6 +163,14 @@ hsg_status hsg_get_couplings_bimodal(hsg_t h, int sample, uint8_t *bits_out);
 hsg_status hsg_set_spins(hsg_t h, int sample, int slot, const float *s);
 hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float *s_out);
 
+/* Every lattice slot of one sample at once, host float32 [R][N][3] (slots
+ * 0 .. R-1, each [N][3] in natural site order), staged in chunks of at most
+ * 256 MiB instead of R calls.  Synchronous like the one-slot calls; the pointer may be pinned or
+ * pageable.  HSG_EINVAL on a NULL argument or a bad sample (nothing stored);
+ * HSG_ENOMEM if the staging buffer cannot be allocated. */
+hsg_status hsg_set_spins_sample(hsg_t h, int sample, const float *s);
+hsg_status hsg_get_spins_sample(hsg_t h, int sample, float *s_out);
+
 /* The same with a caller-owned DEVICE buffer float32 [N][3] (natural site
  * order) on the context's device, e.g. a torch CUDA tensor: enqueued on the
  * configured stream without synchronising, so the buffer must stay valid

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "hsg_get_spins_device": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_couplings_bimodal": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_set_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "hsg_set_spins_sample": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_spins_sample": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "hsg_get_spins": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "hsg_sweep_hb": [ctypes.c_void_p, ctypes.c_int],
     "hsg_sweep_or": [ctypes.c_void_p, ctypes.c_int],
@@ -217,8 +219,13 @@ class Lattice:
 
     # -- data ------------------------------------------------------------
     def set_couplings(self, sample: int, J6) -> None:
-        J6 = np.ascontiguousarray(J6, dtype=np.float32)
-        assert J6.size == self.N(sample) * 18
+        """Couplings float32 [N, 3, 6] from a numpy array or a contiguous CPU
+        torch tensor (pinned or not)."""
+        if hasattr(J6, "data_ptr"):
+            assert J6.is_contiguous() and J6.numel() == self.N(sample) * 18
+        else:
+            J6 = np.ascontiguousarray(J6, dtype=np.float32)
+            assert J6.size == self.N(sample) * 18
         _check(self._lib.hsg_set_couplings(self._h, sample, _ptr(J6)))
 
     def get_couplings(self, sample: int) -> np.ndarray:
@@ -248,6 +255,26 @@ class Lattice:
         if out is None:
             out = np.empty((self.N(sample), 3), dtype=np.float32)
         _check(self._lib.hsg_get_spins(self._h, sample, slot, _ptr(out)))
+        return out
+
+    def set_spins_sample(self, sample: int, s) -> None:
+        """Every lattice slot of a sample from host float32 [R, N, 3] (a numpy
+        array or a contiguous CPU torch tensor, pinned or not)."""
+        if hasattr(s, "data_ptr"):
+            assert s.is_contiguous() and s.numel() == self.R * self.N(sample) * 3
+        else:
+            s = np.ascontiguousarray(s, dtype=np.float32)
+            assert s.size == self.R * self.N(sample) * 3
+        _check(self._lib.hsg_set_spins_sample(self._h, sample, _ptr(s)))
+
+    def get_spins_sample(self, sample: int, out=None):
+        """Every lattice slot of a sample as host float32 [R, N, 3]."""
+        if out is None:
+            out = np.empty((self.R, self.N(sample), 3), dtype=np.float32)
+        else:
+            assert out.is_contiguous() if hasattr(out, "data_ptr") else out.flags.c_contiguous
+            assert (out.numel() if hasattr(out, "data_ptr") else out.size) == self.R * self.N(sample) * 3
+        _check(self._lib.hsg_get_spins_sample(self._h, sample, _ptr(out)))
         return out
 
     # -- Monte Carlo -----------------------------------------------------

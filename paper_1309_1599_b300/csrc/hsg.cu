@@ -17,6 +17,7 @@
 #include "../../include/hsg.h"
 #include "fused.cuh"
 #include "persistent.cuh"
+#include "transfer.cuh"
 #include "sequential.cuh"
 #include "kernels.cuh"
 
@@ -88,6 +89,8 @@ struct hsg_ctx {
   long long* d_pt_acc = nullptr;  // [S][n_rep][max(NT-1,1)]
   uint32_t* d_counters = nullptr; // [0] HB sweeps, [1] PT sweeps
   float* d_stage = nullptr;     // staging for spins [max N][3]
+  float* d_big = nullptr;       // staging for whole-sample transfers (grown on demand)
+  size_t big_cap = 0;           // floats in d_big
   uint32_t* d_tmp_u32 = nullptr;
   bool energy_valid = false;
   uint64_t counters[3] = {0, 0, 0};
@@ -152,6 +155,7 @@ void free_ctx(hsg_ctx* h) {
   cudaFree(h->d_pt_acc);
   cudaFree(h->d_counters);
   cudaFree(h->d_stage);
+  cudaFree(h->d_big);
   cudaFree(h->d_tmp_u32);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -939,30 +943,46 @@ static void decode_bimodal_host(uint8_t bits, float D, float* j) {
   j[5] = d[5];
 }
 
+// Largest staging buffer for whole-sample transfers (floats): 256 MiB.
+constexpr size_t kBigStageFloats = static_cast<size_t>(64) << 20;
+
+// Makes d_big hold min(want, kBigStageFloats) floats (growing it after the
+// stream has drained); returns that count in *got.
+static hsg_status big_stage(hsg_t h, size_t want, size_t* got) {
+  const size_t n = std::min(want, kBigStageFloats);
+  if (h->big_cap < n) {
+    HSG_CUDA(cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_big);
+    h->d_big = nullptr;
+    h->big_cap = 0;
+    HSG_TRY(dalloc(&h->d_big, n));
+    h->big_cap = n;
+  }
+  *got = n;
+  return HSG_OK;
+}
+
 hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
   if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   if (h->prec == HSG_BIMODAL) return fail(HSG_EINVAL, "bimodal contexts take hsg_set_couplings_bimodal");
   Bucket& b = h->buckets[h->sample_bucket[sample]];
-  const size_t N = b.N;
-  std::vector<char> buf(3 * N * bond_bytes(h->prec));
-  if (h->prec == HSG_F32) {
-    float* out = reinterpret_cast<float*>(buf.data());
-    for (size_t i = 0; i < N; ++i)
-      for (int mu = 0; mu < 3; ++mu)
-        for (int e = 0; e < 6; ++e) out[(mu * N + storage_site(i, b.L)) * 6 + e] = J6[(i * 3 + mu) * 6 + e];
-  } else {
-    __half* out = reinterpret_cast<__half*>(buf.data());
-    for (size_t i = 0; i < N; ++i)
-      for (int mu = 0; mu < 3; ++mu) {
-        const size_t d = mu * N + storage_site(i, b.L);
-        for (int e = 0; e < 6; ++e) out[d * 8 + e] = __float2half_rn(J6[(i * 3 + mu) * 6 + e]);
-        out[d * 8 + 6] = __float2half_rn(0.0f);
-        out[d * 8 + 7] = __float2half_rn(0.0f);
-      }
+  const long long N = b.N;
+  // FP32 [N][3][6] to the device in chunks of whole sites; the packing kernel
+  // permutes them to storage order and rounds to the storage precision
+  size_t cap = 0;
+  HSG_TRY(big_stage(h, 18 * static_cast<size_t>(N), &cap));
+  const long long per = static_cast<long long>(cap / 18);
+  void* dst = sample_coupling_ptr(h, sample);
+  for (long long i0 = 0; i0 < N; i0 += per) {
+    const long long n = std::min(per, N - i0);
+    HSG_CUDA(cudaMemcpyAsync(h->d_big, J6 + 18 * i0, sizeof(float) * 18 * n, cudaMemcpyHostToDevice, h->stream));
+    const unsigned blocks = static_cast<unsigned>((3 * n + 255) / 256);
+    if (h->prec == HSG_F32) k_pack_couplings<kPrecF32><<<blocks, 256, 0, h->stream>>>(h->d_big, dst, b.L, i0, n);
+    else k_pack_couplings<kPrecF16><<<blocks, 256, 0, h->stream>>>(h->d_big, dst, b.L, i0, n);
+    HSG_CUDA(cudaGetLastError());
   }
   HSG_CUDA(cudaStreamSynchronize(h->stream));
-  HSG_CUDA(cudaMemcpy(sample_coupling_ptr(h, sample), buf.data(), buf.size(), cudaMemcpyHostToDevice));
   h->energy_valid = false;
   return HSG_OK;
 }
@@ -1055,6 +1075,49 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float* s_out) {
   k_gather_spins<<<(b.N + 255) / 256, 256, 0, h->stream>>>(base, h->d_stage, b.L, h->V, slot % h->V);
   HSG_CUDA(cudaGetLastError());
   HSG_CUDA(cudaMemcpyAsync(s_out, h->d_stage, sizeof(float) * 3 * b.N, cudaMemcpyDeviceToHost, h->stream));
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  return status_check(h);
+}
+
+hsg_status hsg_set_spins_sample(hsg_t h, int sample, const float* s) {
+  if (!h || !s) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  float* spins_s = b.d_spins[b.cur] + static_cast<size_t>(sb) * b.G * 3 * static_cast<size_t>(b.N) * h->V;
+  const long long total = static_cast<long long>(h->R) * b.N;  // (slot, site) records of 3 floats
+  size_t cap = 0;
+  HSG_TRY(big_stage(h, 3 * static_cast<size_t>(total), &cap));
+  const long long per = static_cast<long long>(cap / 3);
+  for (long long q0 = 0; q0 < total; q0 += per) {
+    const long long n = std::min(per, total - q0);
+    HSG_CUDA(cudaMemcpyAsync(h->d_big, s + 3 * q0, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    k_scatter_spins_many<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(h->d_big, spins_s, b.L,
+                                                                                          h->V, q0, n);
+    HSG_CUDA(cudaGetLastError());
+  }
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  h->energy_valid = false;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins_sample(hsg_t h, int sample, float* s_out) {
+  if (!h || !s_out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  Bucket& b = h->buckets[h->sample_bucket[sample]];
+  const int sb = h->sample_local[sample];
+  const float* spins_s = b.d_spins[b.cur] + static_cast<size_t>(sb) * b.G * 3 * static_cast<size_t>(b.N) * h->V;
+  const long long total = static_cast<long long>(h->R) * b.N;
+  size_t cap = 0;
+  HSG_TRY(big_stage(h, 3 * static_cast<size_t>(total), &cap));
+  const long long per = static_cast<long long>(cap / 3);
+  for (long long q0 = 0; q0 < total; q0 += per) {
+    const long long n = std::min(per, total - q0);
+    k_gather_spins_many<<<static_cast<unsigned>((n + 255) / 256), 256, 0, h->stream>>>(spins_s, h->d_big, b.L, h->V,
+                                                                                         q0, n);
+    HSG_CUDA(cudaGetLastError());
+    HSG_CUDA(cudaMemcpyAsync(s_out + 3 * q0, h->d_big, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  }
   HSG_CUDA(cudaStreamSynchronize(h->stream));
   return status_check(h);
 }
