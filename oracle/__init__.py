@@ -29,6 +29,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_*.py``):
                equivariance under global rotations and local gauge
                transformations (pins J versus J^T).
   local_field  equals minus the numerical gradient of ``energy``.
+  site_field   the sum local_field evaluates after gathering a site's bonds
+               and neighbours (one code path), so the same pin holds;
+               neighbour is the gather's index arithmetic.
   bimodal_j9   single-bit cases, the paper's moments over all 128 bytes,
                time reversal, the isotropic limit (test_oracle_bimodal.py).
   energy       beta = 0 moments; high-temperature series to O(beta^3);
@@ -90,6 +93,8 @@ def _load():
                 "oracle_uniform52": (d, [u32, u32]),
                 "oracle_hb_words": (None, [u64, u32, u32, u32, vp]),
                 "oracle_local_field": (None, [i32, vp, vp, ctypes.c_long, vp]),
+                "oracle_site_field": (None, [vp, vp, vp, vp, vp]),
+                "oracle_neighbour": (ctypes.c_long, [i32, ctypes.c_long, i32, i32]),
                 "oracle_energy": (d, [i32, vp, vp]),
                 "oracle_hb_draw": (None, [vp, d, u32, u32, vp]),
                 "oracle_or_update": (None, [vp, vp, vp]),
@@ -195,6 +200,21 @@ def local_field(L: int, J9, s, i: int) -> np.ndarray:
     h = np.zeros(3)
     _load().oracle_local_field(L, _ptr(J9), _ptr(s), i, _ptr(h))
     return h
+
+
+def site_field(Jup, Jdn, s_up, s_dn) -> np.ndarray:
+    """Local field of one site from its own data: Jup[mu] the 3x3 bond to
+    x+mu, Jdn[mu] the bond from x-mu, s_up[mu] / s_dn[mu] the neighbour
+    spins (each [3][3] / [3][9] as arrays of shape (3, 3) or (3, 3, 3))."""
+    Jup, Jdn, s_up, s_dn = _f64(Jup), _f64(Jdn), _f64(s_up), _f64(s_dn)
+    h = np.zeros(3)
+    _load().oracle_site_field(_ptr(Jup), _ptr(Jdn), _ptr(s_up), _ptr(s_dn), _ptr(h))
+    return h
+
+
+def neighbour(L: int, i: int, mu: int, sign: int) -> int:
+    """Natural index of the periodic neighbour of site i along mu."""
+    return int(_load().oracle_neighbour(L, int(i), mu, sign))
 
 
 def fields(L: int, J9, s, colour: int) -> np.ndarray:

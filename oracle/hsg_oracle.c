@@ -168,22 +168,43 @@ static int site_colour(int L, long i) {
 /* with h_x = -dH/ds_x:                                                      */
 /*   h_x = sum_mu [ J_{x,mu} s_{x+mu} + J_{x-mu,mu}^T s_{x-mu} ].            */
 /* ------------------------------------------------------------------------ */
-void oracle_local_field(int L, const double *J9, const double *s, long i,
-                        double h[3]) {
+/* The same sum from the site's own data: Jup[mu] (row-major 3x3) is the
+   bond (x, x+mu), Jdn[mu] the bond (x-mu, x), s_up[mu] and s_dn[mu] the
+   spins at x+mu and x-mu. */
+void oracle_site_field(const double *Jup, const double *Jdn, const double *s_up,
+                       const double *s_dn, double h[3]) {
   h[0] = h[1] = h[2] = 0.0;
   for (int mu = 0; mu < 3; ++mu) {
-    long up = neighbour(L, i, mu, +1);
-    long dn = neighbour(L, i, mu, -1);
-    const double *Jup = J9 + (i * 3 + mu) * 9;  /* bond (i, i+mu) */
-    const double *Jdn = J9 + (dn * 3 + mu) * 9; /* bond (i-mu, i) */
     for (int a = 0; a < 3; ++a) {
       for (int b = 0; b < 3; ++b) {
-        h[a] += Jup[a * 3 + b] * s[up * 3 + b];
-        h[a] += Jdn[b * 3 + a] * s[dn * 3 + b];
+        h[a] += Jup[mu * 9 + a * 3 + b] * s_up[mu * 3 + b];
+        h[a] += Jdn[mu * 9 + b * 3 + a] * s_dn[mu * 3 + b];
       }
     }
   }
 }
+
+void oracle_local_field(int L, const double *J9, const double *s, long i,
+                        double h[3]) {
+  double Jup[27], Jdn[27], s_up[9], s_dn[9];
+  for (int mu = 0; mu < 3; ++mu) {
+    long up = neighbour(L, i, mu, +1);
+    long dn = neighbour(L, i, mu, -1);
+    for (int e = 0; e < 9; ++e) {
+      Jup[mu * 9 + e] = J9[(i * 3 + mu) * 9 + e];   /* bond (i, i+mu) */
+      Jdn[mu * 9 + e] = J9[(dn * 3 + mu) * 9 + e];  /* bond (i-mu, i) */
+    }
+    for (int b = 0; b < 3; ++b) {
+      s_up[mu * 3 + b] = s[up * 3 + b];
+      s_dn[mu * 3 + b] = s[dn * 3 + b];
+    }
+  }
+  oracle_site_field(Jup, Jdn, s_up, s_dn, h);
+}
+
+/* Natural index of the neighbour of site i in direction mu (0, 1, 2 = x, y,
+   z), forward (sign = +1) or backward (sign = -1), periodic. */
+long oracle_neighbour(int L, long i, int mu, int sign) { return neighbour(L, i, mu, sign); }
 
 /* Bimodal couplings (Sec. II.A): the isotropic coupling J = +-1 and the six
    independent entries D^{ab} (a >= b) of the symmetric anisotropy = +-D.

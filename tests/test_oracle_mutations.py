@@ -14,8 +14,8 @@ SRC = os.path.join(ROOT, "oracle", "hsg_oracle.c")
 
 MUTATIONS = {
     # field: J instead of J^T on the backward bond (local gauge, gradient)
-    "field_transpose": ("h[a] += Jdn[b * 3 + a] * s[dn * 3 + b];",
-                        "h[a] += Jdn[a * 3 + b] * s[dn * 3 + b];",
+    "field_transpose": ("h[a] += Jdn[mu * 9 + b * 3 + a] * s_dn[mu * 3 + b];",
+                        "h[a] += Jdn[mu * 9 + a * 3 + b] * s_dn[mu * 3 + b];",
                         ["test_oracle_updates.py"]),
     # heat-bath: density exp(kappa u / 2) instead of exp(kappa u)
     "hb_half_kappa": ("w = -log1p(r0 * expm1(-2.0 * kappa)) / kappa;",

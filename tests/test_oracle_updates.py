@@ -248,3 +248,39 @@ def test_ferromagnet_ground_state_and_low_T():
         if t >= 100:
             es.append(oracle.energy(L, J9, s) / N)
     assert abs(np.mean(es) + 3 - T) < 0.1 * T
+
+
+def test_neighbour_is_periodic_and_inverse():
+    """The gather's index arithmetic: forward and backward steps undo each
+    other, wrap at the faces, and move along x, y, z by 1, L, L^2."""
+    L = 6
+    rng = np.random.default_rng(4)
+    for i in rng.integers(0, L ** 3, 200):
+        for mu in range(3):
+            up = oracle.neighbour(L, i, mu, +1)
+            assert oracle.neighbour(L, up, mu, -1) == i
+            c = [i % L, (i // L) % L, i // (L * L)]
+            c[mu] = (c[mu] + 1) % L
+            assert up == c[0] + L * (c[1] + L * c[2])
+    assert oracle.neighbour(L, L - 1, 0, +1) == 0
+    assert oracle.neighbour(L, 0, 2, -1) == (L - 1) * L * L
+
+
+def test_site_field_from_gathered_data_is_minus_energy_gradient():
+    """site_field on a site's own bonds and neighbours is -dE/ds_x (the
+    energy is linear in one spin, so a unit step gives the derivative)."""
+    L = 4
+    rng = np.random.default_rng(8)
+    J9 = rng.standard_normal((L ** 3, 3, 9))
+    s = rng.standard_normal((L ** 3, 3))
+    for i in (0, 5, 21, 63):
+        Jup = np.stack([J9[i, mu] for mu in range(3)])
+        Jdn = np.stack([J9[oracle.neighbour(L, i, mu, -1), mu] for mu in range(3)])
+        s_up = np.stack([s[oracle.neighbour(L, i, mu, +1)] for mu in range(3)])
+        s_dn = np.stack([s[oracle.neighbour(L, i, mu, -1)] for mu in range(3)])
+        h = oracle.site_field(Jup, Jdn, s_up, s_dn)
+        E0 = oracle.energy(L, J9, s)
+        for a in range(3):
+            t = s.copy()
+            t[i, a] += 1.0
+            assert abs(-(oracle.energy(L, J9, t) - E0) - h[a]) < 1e-9
