@@ -246,6 +246,26 @@ hsg_status hsg_set_counters(hsg_t h, const uint64_t in[3]);
  * (L for whole planes); out[2] = kernel launches per sweep. */
 hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]);
 
+/* Resident steps (persistent contexts) of `sample`'s lattice size: out[0] =
+ * bond residency (0 global, 1 shared as stored, 2 shared as FP32), out[1] =
+ * lattice groups per work item, out[2] = threads per CTA; zeros otherwise. */
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[3]);
+
+/* Autotuner (Sec. III's sweeps; the tiling is free, the results do not
+ * depend on it).  For each lattice size of the context it times the
+ * candidate launch shapes on the context's own couplings and spins and keeps
+ * the fastest: the band height of the fused sweep (timed as overrelaxation
+ * sweeps whose output is discarded) and, for persistent contexts, the groups
+ * per work item and threads per CTA of the resident steps (timed on scratch
+ * copies of the spins, labels, energies and acceptances).  The state is not
+ * changed.  A choice is remembered for the process per (L, lattices per
+ * element, precision, N_T, bond residency), so later contexts of the same
+ * shape take it without timing.  Synchronous; a new shape must beat the
+ * current one by 2% to replace it.  HSG_EINVAL on NULL, HSG_ENOMEM if the
+ * scratch copies cannot be allocated, HSG_ECUDA / HSG_ETIMEOUT from the timed
+ * launches. */
+hsg_status hsg_autotune(hsg_t h);
+
 /* Number of compute kernels this context has enqueued so far (sweeps,
  * energies, PT, measurement and counter updates, including those replayed
  * from graphs; data-transfer helpers are not counted). */

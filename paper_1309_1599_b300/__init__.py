@@ -85,6 +85,8 @@ _SIGNATURES = {
     "hsg_set_counters": [ctypes.c_void_p, ctypes.c_void_p],
     "hsg_get_launch_count": [ctypes.c_void_p, ctypes.c_void_p],
     "hsg_get_sweep_plan": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_get_resident_plan": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hsg_autotune": [ctypes.c_void_p],
     "hsg_save": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_load": [ctypes.c_void_p, ctypes.c_char_p],
     "hsg_synchronize": [ctypes.c_void_p],
@@ -359,6 +361,17 @@ class Lattice:
         out = np.zeros(3, dtype=np.int32)
         _check(self._lib.hsg_get_sweep_plan(self._h, sample, _ptr(out)))
         return {"fused": bool(out[0]), "band_rows": int(out[1]), "launches_per_sweep": int(out[2])}
+
+    def get_resident_plan(self, sample: int = 0) -> dict:
+        out = np.zeros(3, dtype=np.int32)
+        _check(self._lib.hsg_get_resident_plan(self._h, sample, _ptr(out)))
+        return {"bond_residency": int(out[0]), "groups_per_item": int(out[1]), "threads": int(out[2])}
+
+    def autotune(self) -> None:
+        """Time the candidate launch shapes on this context's data and keep
+        the fastest (the state is unchanged; choices are remembered for the
+        process)."""
+        _check(self._lib.hsg_autotune(self._h))
 
     def get_launch_count(self) -> int:
         out = np.zeros(1, dtype=np.uint64)

@@ -7,9 +7,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -90,6 +93,7 @@ struct hsg_ctx {
   uint32_t* d_counters = nullptr; // [0] HB sweeps, [1] PT sweeps
   float* d_stage = nullptr;     // staging for spins [max N][3]
   float* d_big = nullptr;       // staging for whole-sample transfers (grown on demand)
+  size_t fused_smem_attr = 0;   // dynamic shared memory the fused kernels are allowed
   size_t big_cap = 0;           // floats in d_big
   uint32_t* d_tmp_u32 = nullptr;
   bool energy_valid = false;
@@ -476,35 +480,46 @@ hsg_status plan_persistent(hsg_ctx* h) {
 
 hsg_status enqueue_bump(hsg_ctx* h, uint32_t dhb, uint32_t dpt, cudaStream_t st);
 
+// Launch arguments of the resident-step kernel for one bucket (the state
+// buffers of the context; the tuner substitutes scratch copies).
+PersistentParams persistent_params(hsg_ctx* h, const Bucket& b, int steps) {
+  PersistentParams p;
+  p.spins = b.d_spins[b.cur];
+  p.J = b.d_J;
+  p.sample_ids = b.d_samples;
+  p.L = b.L;
+  p.N = b.N;
+  p.G = b.G;
+  p.R = h->R;
+  p.n_rep = h->n_rep;
+  p.NT = h->NT;
+  p.n_or = h->n_or;
+  p.steps = steps;
+  p.beta = h->d_beta;
+  p.E = h->d_E;
+  p.perm = h->d_perm;
+  p.temp_of = h->d_temp_of;
+  p.accepted = h->d_pt_acc;
+  p.key = philox_key(h->seed);
+  p.counters = h->d_counters;
+  p.D = h->bimodal_D;
+  return p;
+}
+
+hsg_status launch_persistent(hsg_ctx* h, const Bucket& b, PersistentParams p, int gp, int threads,
+                             cudaStream_t st) {
+  void* args[] = {&p};
+  *h->launch_sink += 1;
+  HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L, gp), dim3(b.S_b * h->n_rep),
+                            dim3(threads), args, b.res_smem, st));
+  return HSG_OK;
+}
+
 // `steps` whole Monte Carlo steps with every replica set resident in shared
 // memory: one launch per bucket, then the sweep counters advance.
 hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
-  for (const Bucket& b : h->buckets) {
-    PersistentParams p;
-    p.spins = b.d_spins[b.cur];
-    p.J = b.d_J;
-    p.sample_ids = b.d_samples;
-    p.L = b.L;
-    p.N = b.N;
-    p.G = b.G;
-    p.R = h->R;
-    p.n_rep = h->n_rep;
-    p.NT = h->NT;
-    p.n_or = h->n_or;
-    p.steps = steps;
-    p.beta = h->d_beta;
-    p.E = h->d_E;
-    p.perm = h->d_perm;
-    p.temp_of = h->d_temp_of;
-    p.accepted = h->d_pt_acc;
-    p.key = philox_key(h->seed);
-    p.counters = h->d_counters;
-    p.D = h->bimodal_D;
-    void* args[] = {&p};
-    *h->launch_sink += 1;
-    HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L, b.res_gp), dim3(b.S_b * h->n_rep),
-                              dim3(b.res_threads), args, b.res_smem, st));
-  }
+  for (const Bucket& b : h->buckets)
+    HSG_TRY(launch_persistent(h, b, persistent_params(h, b, steps), b.res_gp, b.res_threads, st));
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }
 
@@ -835,6 +850,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   }
 
   if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
+  h->fused_smem_attr = max_fused_smem;
   if (h->persistent) {
     const hsg_status ps = plan_persistent(h);
     if (ps != HSG_OK) return bail(ps);
@@ -1352,6 +1368,221 @@ hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]) {
   out[1] = b.fused ? b.band_rows : 0;
   out[2] = b.fused ? 1 : 2;
   return HSG_OK;
+}
+
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[3]) {
+  if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
+  HSG_TRY(check_sample(h, sample));
+  const Bucket& b = h->buckets[h->sample_bucket[sample]];
+  out[0] = h->persistent ? b.res_js : 0;
+  out[1] = h->persistent ? b.res_gp : 0;
+  out[2] = h->persistent ? b.res_threads : 0;
+  return HSG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: the candidate tilings of each bucket, timed on the context's own
+// couplings and spins without changing its state, the fastest kept and
+// remembered for the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+// (kind, L, V, precision, N_T, bond residency) -> (band rows) or (gp, threads)
+std::map<std::array<int, 6>, std::array<int, 2>> g_tune_cache;
+
+bool tune_lookup(const std::array<int, 6>& key, std::array<int, 2>* val) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const auto it = g_tune_cache.find(key);
+  if (it == g_tune_cache.end()) return false;
+  *val = it->second;
+  return true;
+}
+
+void tune_store(const std::array<int, 6>& key, const std::array<int, 2>& val) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = val;
+}
+
+// Mean device time (ms) of `reps` calls of `launch` after one untimed call.
+template <typename F>
+hsg_status time_ms(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& launch, float* ms) {
+  HSG_TRY(launch());
+  HSG_CUDA(cudaEventRecord(e0, h->stream));
+  for (int r = 0; r < reps; ++r) HSG_TRY(launch());
+  HSG_CUDA(cudaEventRecord(e1, h->stream));
+  HSG_CUDA(cudaEventSynchronize(e1));
+  HSG_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  *ms /= static_cast<float>(reps);
+  return status_check(h);
+}
+
+// Streaming buckets: every band height that tiles L (and whole planes)
+// within the fused kernel's limits, timed as overrelaxation sweeps whose
+// output buffer is discarded (the input buffer stays the state).
+hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
+  const std::array<int, 6> key = {0, b.L, h->V, h->prec, 0, 0};
+  std::array<int, 2> got;
+  std::vector<int> cands;
+  if (tune_lookup(key, &got)) {
+    cands.push_back(got[0]);
+  } else {
+    cands.push_back(b.band_rows);  // the current plan first: ties keep it
+    for (int B = 8; B <= b.L; ++B)
+      if (b.L % B == 0 && B != b.band_rows) cands.push_back(B);
+  }
+  const int mt = fused_max_threads(h->V, h->prec);
+  int best_band = b.band_rows;
+  size_t best_smem = b.fused_smem;
+  float best_ms = -1.0f;
+  for (const int want : cands) {
+    int br = 0;
+    size_t sm = 0;
+    if (!plan_fused(b.L, h->V, mt, want, &br, &sm)) continue;
+    if (sm > h->fused_smem_attr) {
+      if (allow_fused_smem_all(h->V, h->prec, sm) != HSG_OK) return HSG_ECUDA;
+      h->fused_smem_attr = sm;
+    }
+    b.band_rows = br;
+    b.n_bands = b.L / br;
+    b.fused_smem = sm;
+    if (cands.size() == 1) {  // remembered choice: nothing to time
+      best_band = br;
+      best_smem = sm;
+      break;
+    }
+    float ms = 0.0f;
+    HSG_TRY(time_ms(h, e0, e1, 3, [&]() -> hsg_status {
+      HSG_TRY(launch_fused<kOR>(h, b, false, h->stream));
+      b.cur ^= 1;  // keep reading the state; the other buffer is scratch
+      return HSG_OK;
+    }, &ms));
+    // a new choice must win by 2%, so timing noise does not move the plan
+    if (best_ms < 0.0f || ms < 0.98f * best_ms) {
+      best_ms = ms;
+      best_band = br;
+      best_smem = sm;
+    }
+  }
+  b.band_rows = best_band;
+  b.n_bands = b.L / best_band;
+  b.fused_smem = best_smem;
+  tune_store(key, {best_band, 0});
+  return HSG_OK;
+}
+
+// Resident buckets: groups per work item and threads per CTA, timed as
+// stretches of whole steps on scratch copies of the state (spins, labels,
+// energies, acceptances), so the context's state is untouched.
+hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
+  const std::array<int, 6> key = {1, b.L, h->V, h->prec, h->NT, b.res_js};
+  std::array<int, 2> got;
+  if (tune_lookup(key, &got)) {
+    b.res_gp = got[0];
+    b.res_threads = got[1];
+    return HSG_OK;
+  }
+  int dev = 0, optin = 0;
+  HSG_CUDA(cudaGetDevice(&dev));
+  HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t S = h->S, n_spin = static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
+  float* sp = nullptr;
+  int *perm = nullptr, *temp_of = nullptr;
+  double* E = nullptr;
+  long long* acc = nullptr;
+  hsg_status st = dalloc(&sp, n_spin);
+  if (st == HSG_OK) st = dalloc(&perm, S * h->n_rep * h->NT);
+  if (st == HSG_OK) st = dalloc(&temp_of, S * h->R);
+  if (st == HSG_OK) st = dalloc(&E, S * h->R);
+  if (st == HSG_OK) st = dalloc(&acc, S * h->n_rep * acc_stride(h));
+  auto run = [&]() -> hsg_status {
+    HSG_CUDA(cudaMemcpyAsync(sp, b.d_spins[b.cur], n_spin * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    HSG_CUDA(cudaMemcpyAsync(perm, h->d_perm, S * h->n_rep * h->NT * sizeof(int), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    HSG_CUDA(cudaMemsetAsync(acc, 0, S * h->n_rep * acc_stride(h) * sizeof(long long), h->stream));
+    const int steps = (h->measure_every > 0 && h->measure_every <= kMaxStepsPerLaunch) ? h->measure_every : 10;
+    PersistentParams p = persistent_params(h, b, steps);
+    p.spins = sp;
+    p.perm = perm;
+    p.temp_of = temp_of;
+    p.E = E;
+    p.accepted = acc;
+    const int gp_max = persistent_gp(h->V, h->NT, b.res_js, b.L);
+    float best_ms = -1.0f;
+    int best_gp = b.res_gp, best_threads = b.res_threads;
+    std::vector<std::array<int, 2>> cands = {{b.res_gp, b.res_threads}};  // current plan first
+    for (int gp = 1; gp <= gp_max; ++gp)
+      for (const int W : {16, 18, 20, 22, 24, 28, 32})
+        if (gp != b.res_gp || 32 * W != b.res_threads) cands.push_back({gp, 32 * W});
+    for (const auto& c : cands) {
+      void* fn = persistent_kernel(h->V, h->prec, b.res_js, b.L, c[0]);
+      cudaFuncAttributes fa;
+      HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
+      if (c[1] > fa.maxThreadsPerBlock) continue;
+      HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - static_cast<int>(fa.sharedSizeBytes)));
+      int occ = 0;
+      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c[1], b.res_smem));
+      if (occ < 1) continue;
+      float ms = 0.0f;
+      HSG_TRY(time_ms(h, e0, e1, 2, [&]() { return launch_persistent(h, b, p, c[0], c[1], h->stream); }, &ms));
+      if (best_ms < 0.0f || ms < 0.98f * best_ms) {
+        best_ms = ms;
+        best_gp = c[0];
+        best_threads = c[1];
+      }
+    }
+    b.res_gp = best_gp;
+    b.res_threads = best_threads;
+    tune_store(key, {best_gp, best_threads});
+    return HSG_OK;
+  };
+  if (st == HSG_OK) st = run();
+  cudaStreamSynchronize(h->stream);
+  cudaFree(sp);
+  cudaFree(perm);
+  cudaFree(temp_of);
+  cudaFree(E);
+  cudaFree(acc);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+hsg_status hsg_autotune(hsg_t h) {
+  if (!h) return fail(HSG_EINVAL, "handle is NULL");
+  HSG_CUDA(cudaStreamSynchronize(h->stream));
+  HSG_TRY(status_check(h));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HSG_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaGetLastError();
+    return fail(HSG_ECUDA, "cudaEventCreate failed");
+  }
+  uint64_t* sink = h->launch_sink;
+  uint64_t scratch_launches = 0;
+  h->launch_sink = &scratch_launches;  // tuning launches are not the run's
+  hsg_status st = HSG_OK;
+  for (Bucket& b : h->buckets) {
+    if (st == HSG_OK && b.fused) st = tune_fused(h, b, e0, e1);
+    if (st == HSG_OK && h->persistent) st = tune_persistent(h, b, e0, e1);
+  }
+  h->launch_sink = sink;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the captured step graphs hold the old launch shapes
+  for (int a = 0; a < 2; ++a)
+    for (int m = 0; m < 2; ++m)
+      if (h->g_step[a][m]) {
+        cudaGraphExecDestroy(h->g_step[a][m]);
+        h->g_step[a][m] = nullptr;
+      }
+  return st;
 }
 
 hsg_status hsg_get_launch_count(hsg_t h, uint64_t* out) {

@@ -88,6 +88,8 @@ def test_null_arguments_rejected(lib):
     assert lib.hsg_set_couplings_bimodal(None, 0, None) == 1
     assert lib.hsg_get_couplings_bimodal(None, 0, None) == 1
     assert lib.hsg_set_spins_sample(None, 0, None) == 1
+    assert lib.hsg_autotune(None) == 1
+    assert lib.hsg_get_resident_plan(None, 0, None) == 1
     assert lib.hsg_get_spins_sample(None, 0, None) == 1
     lib.hsg_destroy(None)
 
