@@ -254,12 +254,15 @@ hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[3]);
 /* Autotuner (Sec. III's sweeps; the tiling is free, the results do not
  * depend on it).  For each lattice size of the context it times the
  * candidate launch shapes on the context's own couplings and spins and keeps
- * the fastest: the band height of the fused sweep (timed as overrelaxation
- * sweeps whose output is discarded) and, for persistent contexts, the groups
+ * the fastest: the band height of the fused sweep, or the two-pass
+ * half-sweeps instead (timed as overrelaxation sweeps whose output is
+ * discarded, or that run on a copy of the state) and, for persistent
+ * contexts, the groups
  * per work item and threads per CTA of the resident steps (timed on scratch
  * copies of the spins, labels, energies and acceptances).  The state is not
  * changed.  A choice is remembered for the process per (L, lattices per
- * element, precision, N_T, bond residency), so later contexts of the same
+ * element, precision, lattices of that L, N_T, bond residency), so later
+ * contexts of the same
  * shape take it without timing.  Synchronous; a new shape must beat the
  * current one by 2% to replace it.  HSG_EINVAL on NULL, HSG_ENOMEM if the
  * scratch copies cannot be allocated, HSG_ECUDA / HSG_ETIMEOUT from the timed

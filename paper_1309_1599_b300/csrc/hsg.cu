@@ -1421,9 +1421,12 @@ hsg_status time_ms(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& lau
 
 // Streaming buckets: every band height that tiles L (and whole planes)
 // within the fused kernel's limits, timed as overrelaxation sweeps whose
-// output buffer is discarded (the input buffer stays the state).
+// output buffer is discarded (the input buffer stays the state), and the
+// two-pass half-sweeps (band 0), timed on a copy of the state in the other
+// buffer.  The two-pass kernel wins where the fused z-march has too few
+// CTAs to fill the GPU (few small lattices).
 hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
-  const std::array<int, 6> key = {0, b.L, h->V, h->prec, 0, 0};
+  const std::array<int, 6> key = {0, b.L, h->V, h->prec, b.S_b * h->R, 0};
   std::array<int, 2> got;
   std::vector<int> cands;
   if (tune_lookup(key, &got)) {
@@ -1432,12 +1435,35 @@ hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
     cands.push_back(b.band_rows);  // the current plan first: ties keep it
     for (int B = 8; B <= b.L; ++B)
       if (b.L % B == 0 && B != b.band_rows) cands.push_back(B);
+    cands.push_back(0);
   }
   const int mt = fused_max_threads(h->V, h->prec);
   int best_band = b.band_rows;
   size_t best_smem = b.fused_smem;
   float best_ms = -1.0f;
   for (const int want : cands) {
+    if (want == 0) {  // the two-pass half-sweeps
+      if (cands.size() == 1) {
+        best_band = 0;
+        break;
+      }
+      const size_t bytes = sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
+      HSG_CUDA(cudaMemcpyAsync(b.d_spins[b.cur ^ 1], b.d_spins[b.cur], bytes, cudaMemcpyDeviceToDevice,
+                               h->stream));
+      b.cur ^= 1;
+      float ms = 0.0f;
+      const hsg_status st = time_ms(h, e0, e1, 3, [&]() -> hsg_status {
+        HSG_TRY(launch_half<kOR>(h, b, 0, false, h->stream));
+        return launch_half<kOR>(h, b, 1, false, h->stream);
+      }, &ms);
+      b.cur ^= 1;
+      HSG_TRY(st);
+      if (best_ms < 0.0f || ms < 0.98f * best_ms) {
+        best_ms = ms;
+        best_band = 0;
+      }
+      continue;
+    }
     int br = 0;
     size_t sm = 0;
     if (!plan_fused(b.L, h->V, mt, want, &br, &sm)) continue;
@@ -1466,9 +1492,13 @@ hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
       best_smem = sm;
     }
   }
-  b.band_rows = best_band;
-  b.n_bands = b.L / best_band;
-  b.fused_smem = best_smem;
+  if (best_band == 0) {
+    b.fused = false;  // the state stays in the current buffer
+  } else {
+    b.band_rows = best_band;
+    b.n_bands = b.L / best_band;
+    b.fused_smem = best_smem;
+  }
   tune_store(key, {best_band, 0});
   return HSG_OK;
 }

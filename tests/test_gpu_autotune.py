@@ -16,10 +16,14 @@ def _snapshot(lat):
     return state(lat), lat.get_perm().copy(), lat.get_counters().copy(), lat.get_launch_count()
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_autotune_keeps_state_and_trajectories(persistent):
-    Ls = [8, 12] if persistent else [32, 40]
-    betas = gi.linear_betas(0.3, 1.1, 8)
+@pytest.mark.parametrize("Ls,NT,persistent", [
+    ([32, 40], 8, False),
+    ([8, 12], 8, True),
+    # one small lattice: a handful of CTAs, where the two-pass sweep can win
+    ([16], 4, False),
+])
+def test_autotune_keeps_state_and_trajectories(Ls, NT, persistent):
+    betas = gi.linear_betas(0.3, 1.1, NT)
     kw = dict(n_rep=2, prec=hsg.F16, layout=hsg.BATCHED, n_or=3, measure_every=2, persistent=persistent)
     a, _ = make(Ls, betas, **kw)
     b, _ = make(Ls, betas, **kw)
