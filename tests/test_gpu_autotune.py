@@ -21,6 +21,8 @@ def _snapshot(lat):
     ([8, 12], 8, True),
     # one small lattice: a handful of CTAs, where the two-pass sweep can win
     ([16], 4, False),
+    # mixed: the small bucket may switch to two-pass while L = 64 stays fused
+    ([16, 64], 4, False),
 ])
 def test_autotune_keeps_state_and_trajectories(Ls, NT, persistent):
     betas = gi.linear_betas(0.3, 1.1, NT)
