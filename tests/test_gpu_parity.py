@@ -258,6 +258,8 @@ FUSED_CASES = [
     # the fused sweep (band_rows 0: the library's choice)
     ([8, 12], 2, hsg.F32, hsg.PLAIN, 0),
     ([16], 2, hsg.F16, hsg.BATCHED, 0),
+    ([24], 1, hsg.F16, hsg.BATCHED, 0),                # whole planes
+    ([24], 1, hsg.F16, hsg.BATCHED, 8),
     ([32], 1, hsg.F16, hsg.BATCHED, 0),
     ([32], 1, hsg.F16, hsg.BATCHED, 16),
     ([40], 1, hsg.F16, hsg.BATCHED, 0),
