@@ -113,14 +113,18 @@ typedef struct {
   int band_rows;          /* fused sweep: rows per CTA band, 0 = library choice;
                              otherwise L or a divisor of L >= 8 that fits the
                              block and shared-memory limits (HSG_EINVAL if not) */
-  int persistent;         /* 1: hsg_run_steps keeps every replica set (the N_T
-                             lattices of one replica of one sample) resident in
-                             shared memory and runs whole steps, PT included,
-                             in one launch per stretch of steps between
-                             measurements; needs N_T <= 64, N_T a multiple of
-                             the layout's lattices per element, and
-                             12 N_T L^3 bytes <= 224 KiB for every L
-                             (HSG_EINVAL otherwise).  0: streaming steps. */
+  int persistent;         /* 1: hsg_run_steps keeps the lattices resident in
+                             shared memory.  Where a replica set (the N_T
+                             lattices of one replica of one sample) fits in
+                             one CTA, whole steps, PT included, run in one
+                             launch per stretch of steps between measurements;
+                             otherwise each CTA holds part of a set for one
+                             step and the PT sweep follows as its own kernel.
+                             Needs N_T <= 64, N_T a multiple of the layout's
+                             lattices per element, and one lattice group,
+                             12 V L^3 bytes (V = 1 plain, 2 batched), within
+                             224 KiB for every L (HSG_EINVAL otherwise).
+                             0: streaming steps. */
   double bimodal_D;       /* HSG_BIMODAL: the magnitude D >= 0 of the
                              anisotropic couplings (the paper uses 0.5 and 1);
                              ignored by the other formats */
@@ -248,8 +252,9 @@ hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]);
 
 /* Resident steps (persistent contexts) of `sample`'s lattice size: out[0] =
  * bond residency (0 global, 1 shared as stored, 2 shared as FP32), out[1] =
- * lattice groups per work item, out[2] = threads per CTA; zeros otherwise. */
-hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[3]);
+ * lattice groups per work item, out[2] = threads per CTA, out[3] = lattice
+ * groups per CTA (N_T / V: whole replica sets); zeros otherwise. */
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]);
 
 /* Autotuner (Sec. III's sweeps; the tiling is free, the results do not
  * depend on it).  For each lattice size of the context it times the

@@ -363,9 +363,10 @@ class Lattice:
         return {"fused": bool(out[0]), "band_rows": int(out[1]), "launches_per_sweep": int(out[2])}
 
     def get_resident_plan(self, sample: int = 0) -> dict:
-        out = np.zeros(3, dtype=np.int32)
+        out = np.zeros(4, dtype=np.int32)
         _check(self._lib.hsg_get_resident_plan(self._h, sample, _ptr(out)))
-        return {"bond_residency": int(out[0]), "groups_per_item": int(out[1]), "threads": int(out[2])}
+        return {"bond_residency": int(out[0]), "groups_per_item": int(out[1]), "threads": int(out[2]),
+                "groups_per_cta": int(out[3])}
 
     def autotune(self) -> None:
         """Time the candidate launch shapes on this context's data and keep

@@ -63,6 +63,7 @@ struct Bucket {
   size_t res_smem = 0;        // resident steps: dynamic shared memory per CTA
   int res_gp = 1;             // resident steps: lattice groups per work item
   int res_threads = 512;      // resident steps: threads per CTA
+  int res_gsub = 0;           // resident steps: lattice groups per CTA (N_T/V: whole sets)
 };
 
 }  // namespace
@@ -103,6 +104,7 @@ struct hsg_ctx {
   uint64_t g_step_launches[2][2] = {{0, 0}, {0, 0}};  // kernels per graph replay
   int* d_status = nullptr;     // device status word (HSG_ETIMEOUT from bounded waits)
   bool persistent = false;     // run_steps keeps replica sets resident in shared memory
+  bool res_split = false;      // some replica set spans several CTAs: one step per launch, PT outside
   long long timeout_cycles = 0;
   int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
@@ -380,9 +382,13 @@ bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t*
 
 // Resident-step kernel for (V, precision, bond residency, L, groups per
 // item): L = 8 and 12 have compile-time specialisations when the bonds are
-// resident, and with two lattices per element also two-group items (gp = 2).
+// resident, and with two lattices per element also two-group items (gp = 2);
+// L = 16 and 20 have them for every bond residency.
 template <int V, int PREC, int JS>
 void* persistent_fn_L(int L, int gp) {
+  // L = 16 and 20: parts of replica sets (one or two groups per CTA)
+  if (L == 16) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 16>);
+  if (L == 20) return reinterpret_cast<void*>(k_persistent<V, PREC, JS, 20>);
   if constexpr (JS == 0) {
     return reinterpret_cast<void*>(k_persistent<V, PREC, 0, 0>);
   } else {
@@ -413,9 +419,9 @@ void* persistent_kernel(int V, int prec, int js, int L, int gp) {
 }
 
 // Lattice groups per work item of the resident kernel: two where a
-// specialisation exists and the groups of a replica set pair up.
-int persistent_gp(int V, int NT, int js, int L) {
-  return (V == 2 && js != 0 && (L == 8 || L == 12) && (NT / V) % 2 == 0) ? 2 : 1;
+// specialisation exists and the groups a CTA holds pair up.
+int persistent_gp(int V, int g_sub, int js, int L) {
+  return (V == 2 && js != 0 && (L == 8 || L == 12) && g_sub % 2 == 0) ? 2 : 1;
 }
 
 // Threads of a resident CTA: 512 for the generic kernel; for an L
@@ -438,44 +444,61 @@ int persistent_threads(int items, int hN, int max_threads) {
   return 32 * best_w;
 }
 
-// Plans the resident steps of every bucket: spins 12 N_T N bytes, plus the
-// bonds (3 N per sample) when they fit beside them -- converted to FP32
-// (JS = 2) unless that lowers the CTAs per SM, else as stored (JS = 1) -- or
-// read from global memory (JS = 0).
+// Plans the resident steps of every bucket.  A CTA holds G_sub lattice groups
+// of one replica set: the whole set (N_T/V groups) when it fits, so PT runs
+// in the kernel; otherwise the divisor of the set that keeps the most groups
+// resident per SM (ties: more CTAs per SM), one step per launch with PT
+// outside.  Shared memory per CTA: spins 12 V G_sub N bytes, plus the bonds
+// (3 N per sample) when they fit beside them -- converted to FP32 (JS = 2)
+// unless that lowers the CTAs per SM, else as stored (JS = 1) -- or read from
+// global memory (JS = 0).
 hsg_status plan_persistent(hsg_ctx* h) {
   int dev = 0, optin = 0;
   HSG_CUDA(cudaGetDevice(&dev));
   HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int G_set = h->NT / h->V;
+  h->res_split = false;
   for (Bucket& b : h->buckets) {
-    const size_t spins = static_cast<size_t>(12) * h->NT * b.N;
     const size_t stored = h->prec == HSG_F16 ? 12 : h->prec == HSG_BIMODAL ? 1 : 24;
     const size_t bond_bytes[3] = {0, stored, 24};
-    int best_js = -1, best_occ = 0, best_threads = 0;
+    int best_js = -1, best_occ = 0, best_threads = 0, best_gsub = 0;
     size_t best_smem = 0;
-    for (int js = (h->prec == HSG_F32 ? 1 : 2); js >= 0; --js) {
-      const int gp = persistent_gp(h->V, h->NT, js, b.L);
-      void* fn = persistent_kernel(h->V, h->prec, js, b.L, gp);
-      cudaFuncAttributes fa;
-      HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
-      const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
-      const size_t smem = spins + 3 * static_cast<size_t>(b.N) * bond_bytes[js];
-      if (smem > budget) continue;
-      HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(budget)));
-      int occ = 0;
-      const int threads = persistent_threads(h->NT / h->V / gp, b.N / 2, fa.maxThreadsPerBlock);
-      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
-      if (occ > best_occ) {
-        best_js = js;
-        best_occ = occ;
-        best_smem = smem;
-        best_threads = threads;
+    for (int g_sub = G_set; g_sub >= 1; --g_sub) {
+      if (G_set % g_sub != 0) continue;
+      if (best_js >= 0 && best_gsub == G_set) break;  // a whole set fits: keep PT in the kernel
+      const size_t spins = static_cast<size_t>(12) * h->V * g_sub * b.N;
+      for (int js = (h->prec == HSG_F32 ? 1 : 2); js >= 0; --js) {
+        const int gp = persistent_gp(h->V, g_sub, js, b.L);
+        void* fn = persistent_kernel(h->V, h->prec, js, b.L, gp);
+        cudaFuncAttributes fa;
+        HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
+        const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+        const size_t smem = spins + 3 * static_cast<size_t>(b.N) * bond_bytes[js];
+        if (smem > budget) continue;
+        HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(budget)));
+        int occ = 0;
+        const int threads = persistent_threads(g_sub / gp, b.N / 2, fa.maxThreadsPerBlock);
+        HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
+        if (occ < 1) continue;
+        // groups resident per SM first, then CTAs per SM
+        const long score = static_cast<long>(occ) * g_sub * 1024 + occ;
+        const long best = static_cast<long>(best_occ) * best_gsub * 1024 + best_occ;
+        if (best_js < 0 || score > best) {
+          best_js = js;
+          best_occ = occ;
+          best_smem = smem;
+          best_threads = threads;
+          best_gsub = g_sub;
+        }
       }
     }
-    if (best_js < 0) return fail(HSG_EINVAL, "a replica set does not fit in shared memory");
+    if (best_js < 0) return fail(HSG_EINVAL, "a lattice group does not fit in shared memory");
     b.res_js = best_js;
     b.res_smem = best_smem;
-    b.res_gp = persistent_gp(h->V, h->NT, best_js, b.L);
+    b.res_gsub = best_gsub;
+    b.res_gp = persistent_gp(h->V, best_gsub, best_js, b.L);
     b.res_threads = best_threads;
+    if (best_gsub < G_set) h->res_split = true;
   }
   return HSG_OK;
 }
@@ -505,6 +528,8 @@ PersistentParams persistent_params(hsg_ctx* h, const Bucket& b, int steps) {
   p.key = philox_key(h->seed);
   p.counters = h->d_counters;
   p.D = h->bimodal_D;
+  p.G_sub = b.res_gsub;
+  p.pt = h->res_split ? 0 : 1;
   return p;
 }
 
@@ -512,16 +537,23 @@ hsg_status launch_persistent(hsg_ctx* h, const Bucket& b, PersistentParams p, in
                              cudaStream_t st) {
   void* args[] = {&p};
   *h->launch_sink += 1;
-  HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L, gp), dim3(b.S_b * h->n_rep),
-                            dim3(threads), args, b.res_smem, st));
+  const int n_sub = h->NT / h->V / p.G_sub;  // CTAs per replica set
+  HSG_CUDA(cudaLaunchKernel(persistent_kernel(h->V, h->prec, b.res_js, b.L, gp),
+                            dim3(b.S_b * h->n_rep * n_sub), dim3(threads), args, b.res_smem, st));
   return HSG_OK;
 }
 
-// `steps` whole Monte Carlo steps with every replica set resident in shared
-// memory: one launch per bucket, then the sweep counters advance.
+hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st);
+
+// `steps` whole Monte Carlo steps with the lattices resident in shared
+// memory: one launch per bucket (and, when replica sets span several CTAs,
+// one step per call with the PT sweep as its own kernel), then the sweep
+// counters advance.
 hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
+  if (h->res_split && steps != 1) return fail(HSG_ESTATE, "split replica sets run one step per launch");
   for (const Bucket& b : h->buckets)
     HSG_TRY(launch_persistent(h, b, persistent_params(h, b, steps), b.res_gp, b.res_threads, st));
+  if (h->res_split) HSG_TRY(enqueue_pt(h, st));
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }
 
@@ -724,10 +756,12 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     if (cfg->n_temps > kMaxTempsResident) return fail(HSG_EINVAL, "persistent steps need n_temps <= 64");
     if (cfg->layout == HSG_LAYOUT_BATCHED && cfg->n_temps % 2 != 0)
       return fail(HSG_EINVAL, "persistent steps need n_temps to be a multiple of the lattices per element");
+    // the smallest resident unit is one lattice group (V lattices)
+    const size_t vl = cfg->layout == HSG_LAYOUT_BATCHED ? 2 : 1;
     for (int s = 0; s < cfg->n_samples; ++s) {
       const size_t Ls = cfg->L[s];
-      if (12 * static_cast<size_t>(cfg->n_temps) * Ls * Ls * Ls > 224 * 1024)
-        return fail(HSG_EINVAL, "a replica set (12 n_temps L^3 bytes) does not fit in shared memory");
+      if (12 * vl * Ls * Ls * Ls > 224 * 1024)
+        return fail(HSG_EINVAL, "a lattice group (12 V L^3 bytes) does not fit in shared memory");
     }
   }
   for (int s = 0; s < cfg->n_samples; ++s) {
@@ -1300,8 +1334,9 @@ hsg_status hsg_run_steps(hsg_t h, int n_steps) {
   if (h->persistent) {
     int left = n_steps;
     while (left > 0) {
-      // bounded launches: at most kMaxStepsPerLaunch steps each
-      int k = std::min(left, kMaxStepsPerLaunch);
+      // bounded launches: at most kMaxStepsPerLaunch steps each, one when
+      // replica sets span several CTAs (PT between launches)
+      int k = std::min(left, h->res_split ? 1 : kMaxStepsPerLaunch);
       if (h->measure_every > 0) {
         const uint64_t m = static_cast<uint64_t>(h->measure_every);
         k = static_cast<int>(std::min<uint64_t>(k, m - h->counters[2] % m));
@@ -1372,13 +1407,14 @@ hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]) {
   return HSG_OK;
 }
 
-hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[3]) {
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]) {
   if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   const Bucket& b = h->buckets[h->sample_bucket[sample]];
   out[0] = h->persistent ? b.res_js : 0;
   out[1] = h->persistent ? b.res_gp : 0;
   out[2] = h->persistent ? b.res_threads : 0;
+  out[3] = h->persistent ? b.res_gsub : 0;
   return HSG_OK;
 }
 
@@ -1509,7 +1545,7 @@ hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
 // stretches of whole steps on scratch copies of the state (spins, labels,
 // energies, acceptances), so the context's state is untouched.
 hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
-  const std::array<int, 6> key = {1, b.L, h->V, h->prec, h->NT, b.res_js};
+  const std::array<int, 6> key = {1, b.L, h->V, h->prec, h->NT * 256 + b.res_gsub, b.res_js};
   std::array<int, 2> got;
   if (tune_lookup(key, &got)) {
     b.res_gp = got[0];
@@ -1541,7 +1577,7 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
     p.temp_of = temp_of;
     p.E = E;
     p.accepted = acc;
-    const int gp_max = persistent_gp(h->V, h->NT, b.res_js, b.L);
+    const int gp_max = persistent_gp(h->V, b.res_gsub, b.res_js, b.L);
     float best_ms = -1.0f;
     int best_gp = b.res_gp, best_threads = b.res_threads;
     std::vector<std::array<int, 2>> cands = {{b.res_gp, b.res_threads}};  // current plan first

@@ -7,7 +7,9 @@
 // A CTA owns one replica set: the N_T lattices of one replica index of one
 // sample (all temperatures).  Parallel tempering only exchanges temperatures
 // inside a replica set (App. A.1), so each CTA runs its own PT sweep after its
-// own energies; no CTA ever waits for another.
+// own energies; no CTA ever waits for another.  Where a whole set does not
+// fit (L = 16 to 24), a CTA holds G_sub of its lattice groups for one step:
+// the launch writes their energies and the caller runs the PT sweep.
 //
 // Shared-memory layout.  Global memory keeps each row's sites split by x
 // parity (the streaming kernels' order).  In shared memory the sites are split
@@ -48,11 +50,14 @@ constexpr int kPersistentMaxThreads = 1024;
 
 // Launch bounds of the L specialisations: L = 12 runs one CTA per SM (its
 // spins alone take 166 KB at 8 temperatures) and may use up to 102
-// registers a thread at 640 threads; L = 8 runs two CTAs of 512 threads.
+// registers a thread at 640 threads; L = 8 runs two CTAs of 512 threads, and
+// so does L = 16 (one 98 KB lattice group per CTA).
 template <int LT>
-constexpr int persistent_max_threads() { return LT == 12 ? 640 : LT == 8 ? 512 : kPersistentMaxThreads; }
+constexpr int persistent_max_threads() {
+  return LT == 12 ? 640 : (LT == 8 || LT == 16) ? 512 : kPersistentMaxThreads;
+}
 template <int LT>
-constexpr int persistent_min_blocks() { return LT == 8 ? 2 : 1; }
+constexpr int persistent_min_blocks() { return (LT == 8 || LT == 16) ? 2 : 1; }
 constexpr int kMaxTempsResident = 64;
 constexpr int kMaxStepsPerLaunch = 256;
 
@@ -70,6 +75,10 @@ struct PersistentParams {
   uint2 key;
   const uint32_t* counters;  // [0] heat-bath sweeps, [1] PT sweeps (at launch)
   float D;                 // bimodal couplings: magnitude of the anisotropy
+  int G_sub;               // lattice groups per CTA: N_T/V (a whole replica set)
+                           // or a divisor of it
+  int pt;                  // 1: PT in the kernel (G_sub = N_T/V); 0: one step per
+                           // launch, energies out, the PT sweep by the caller
 };
 
 
@@ -365,18 +374,25 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
   __shared__ int s_perm[kMaxTempsResident];         // temperature -> local lattice
   __shared__ int s_acc[kMaxTempsResident];
 
-  const int sb = blockIdx.x / p.n_rep, r = blockIdx.x - sb * p.n_rep;
-  const int sg = p.sample_ids[sb];
   const int NT = p.NT;
+  const int G_sub = p.G_sub;                              // groups held by this CTA
+  const int n_sub = NT / V / G_sub;                       // CTAs per replica set
+  const bool whole = p.pt != 0;                           // whole replica set, PT here
+  const int NT_loc = G_sub * V;                           // lattices held by this CTA
+  const int sr = blockIdx.x / n_sub, part = blockIdx.x - sr * n_sub;
+  const int sb = sr / p.n_rep, r = sr - sb * p.n_rep;
+  const int sg = p.sample_ids[sb];
   const int L = LT > 0 ? LT : p.L;
   const int N = L * L * L;
-  const int G_set = NT / V;                               // groups of this replica set
-  float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * G_set) * 3 * N * V;
+  float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * (NT / V) +
+                          static_cast<size_t>(part) * G_sub) * 3 * N * V;
   const void* Jg = sample_bonds<PREC>(p.J, sb, N);
-  void* Js = sp + static_cast<size_t>(NT) * 3 * N;        // after the spins (16-byte aligned)
-  const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(r * NT);
+  void* Js = sp + static_cast<size_t>(NT_loc) * 3 * N;    // after the spins (16-byte aligned)
+  const int loc0 = r * NT + part * NT_loc;                // first local lattice's slot
+  const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(loc0);
   const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
+  const int G_set = G_sub;                                // groups swept by this CTA
   const ResidentWarps rw = resident_warps(G_set / GP);
 
   // replica set -> shared memory, parity-split rows -> colour split; one
@@ -422,7 +438,8 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
     const int k = threadIdx.x;
     const int slot = p.perm[(static_cast<size_t>(sg) * p.n_rep + r) * NT + k];
     s_perm[k] = slot - r * NT;
-    s_beta_lat[slot - r * NT] = static_cast<float>(p.beta[k]);
+    const int li = slot - loc0;
+    if (li >= 0 && li < NT_loc) s_beta_lat[li] = static_cast<float>(p.beta[k]);
     s_acc[k] = 0;
   }
   __syncthreads();
@@ -455,15 +472,16 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
     }
     __syncthreads();
     // energies of the local lattices, fixed-order sums of the warp partials
-    if (threadIdx.x < NT) {
+    if (threadIdx.x < NT_loc) {
       const int g = threadIdx.x / V, v = threadIdx.x - g * V;
       double e = 0.0;
       for (int w = 0; w < rw.wpg; ++w) e += s_part[(g * rw.wpg + w) * V + v];
       s_E[threadIdx.x] = e;
     }
     __syncthreads();
-    // parallel tempering within the replica set (App. A.1)
-    if (threadIdx.x == 0 && NT > 1) {
+    // parallel tempering within the replica set (App. A.1), when this CTA
+    // holds all of it
+    if (whole && threadIdx.x == 0 && NT > 1) {
       const uint32_t tp = t_pt0 + static_cast<uint32_t>(step);
       for (int k = 0; k + 1 < NT; ++k) {
         const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(k), gset, tp, kTagTempering), p.key);
@@ -490,7 +508,9 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
       dst[q] = src[gc * N + colour_split_index(i, L, N)];
     }
   }
-  if (threadIdx.x < NT) {
+  if (!whole) {  // part of a replica set: its energies only; PT follows
+    if (threadIdx.x < NT_loc) p.E[static_cast<size_t>(sg) * p.R + loc0 + threadIdx.x] = s_E[threadIdx.x];
+  } else if (threadIdx.x < NT) {
     const int k = threadIdx.x;
     const size_t pbase = (static_cast<size_t>(sg) * p.n_rep + r) * NT;
     p.perm[pbase + k] = s_perm[k] + r * NT;

@@ -22,6 +22,12 @@ CASES = [
     ([8, 12], 4, 2, hsg.F16, hsg.BATCHED, 0, 2, 4),
     # three lattice groups per replica set: one group per work item
     ([8, 12], 6, 2, hsg.F16, hsg.BATCHED, 2, 2, 4),
+    # replica sets larger than shared memory: parts of a set per CTA, one
+    # step per launch, PT as its own kernel
+    ([16], 8, 2, hsg.F16, hsg.BATCHED, 3, 2, 5),
+    ([20], 4, 2, hsg.F32, hsg.PLAIN, 2, 2, 4),
+    # mixed: L = 8 sets would fit whole, but L = 16 makes every step split
+    ([16, 8], 4, 2, hsg.F16, hsg.BATCHED, 2, 2, 4),
 ]
 
 
