@@ -65,8 +65,8 @@ NCU_TRAFFIC = {
     # profiles/k_sweep_fused_or_L64_S1_R64_f16.md: 391.3 MB for one sample, x8 samples
     ("21c7c0fc81184452", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3130345472,
     # profiles/k_persistent_L8x256_L12x256_R32_f16.md: both launches of 10 MCS
-    ("fb8181e036b27878", "L8x256_L12x256_R32_f16",
-     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361460480,
+    ("65cd35adf56a9764", "L8x256_L12x256_R32_f16",
+     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361584128,
 }
 
 
