@@ -51,10 +51,15 @@ WORKLOADS = {
     # memory (4 replicas x 8 temperatures per sample)
     "L8x256_L12x256_R32_f16": dict(Ls=(8,) * 256 + (12,) * 256, S=512, n_rep=4, NT=8, Tmin=0.2,
                                    Tmax=0.8, n_or=8, measure_every=10, persistent=True),
+    # mid-size lattices: a replica set (393 KB) is larger than shared memory,
+    # so each CTA holds one lattice group for one step and PT runs between
+    "L16_S512_R32_f16": dict(L=16, S=512, n_rep=2, NT=16, Tmin=0.15, Tmax=0.75, n_or=8,
+                             measure_every=10, persistent=True),
 }
 DEFAULT_WORKLOAD = "L64_S8_R64_f16"
-# the small-lattice workload summarised in every run of another workload
+# the small- and mid-size-lattice workloads summarised in every run of another workload
 SMALL_WORKLOAD = "L8x256_L12x256_R32_f16"
+MID_WORKLOAD = "L16_S512_R32_f16"
 
 # DRAM bytes per launch of the dominant kernel from an ncu capture, keyed by a
 # hash of the device sources that kernel is built from (stale -> null), the
@@ -288,10 +293,11 @@ def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
 
 
 def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3):
-    """Device time of the resident-step kernels for 10 whole MCS without
-    measurement (one launch per distinct L + one counter bump of ~2 us),
-    from CUDA events on the library's stream; returns (ms per 10 MCS,
-    launches per 10 MCS)."""
+    """Device time of the resident steps for 10 whole MCS without
+    measurement, from CUDA events on the library's stream: one launch per
+    distinct L plus a counter bump of ~2 us, or, where replica sets span
+    several CTAs, per MCS one launch per L, the PT sweep and the bump.
+    Returns (ms per 10 MCS, launches per 10 MCS)."""
     samples, J, spins, beta = inputs
     wk = dict(w, measure_every=0)
     lat = build_lattice(hsg, wk, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=True)
@@ -306,8 +312,7 @@ def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3):
         lat.run_steps(MCS_PER_STEP)
     e1.record(stream)
     torch.cuda.synchronize()
-    n_kernels = (lat.get_launch_count() - l0) // n_calls - 1
-    assert n_kernels == len(set(sample_Ls(w)))
+    n_kernels = (lat.get_launch_count() - l0) // n_calls
     lat.destroy()
     return e0.elapsed_time(e1) / n_calls, n_kernels
 
@@ -361,16 +366,20 @@ def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampl
         fpu = flops_per_update(w["n_or"])
         achieved = upd * fpu / (k_ms * 1e-3) / 1e12
         vname = 2 if layout == hsg.BATCHED else 1
-        roof = {"bound": "alu",
-                "kernel": f"k_persistent<{vname},f16> ({MCS_PER_STEP} MCS per launch, one launch per L)",
+        # replica sets that span several CTAs run one MCS per launch, PT between
+        split = any(t["groups_per_cta"] * vname < w["NT"] for t in tiling.values())
+        n_res = len(tiling) * (MCS_PER_STEP if split else 1)
+        kname = (f"k_persistent<{vname},f16> (1 MCS per launch, parts of replica sets, PT kernel between)"
+                 if split else f"k_persistent<{vname},f16> ({MCS_PER_STEP} MCS per launch, one launch per L)")
+        roof = {"bound": "alu", "kernel": kname,
                 "achieved": round(achieved, 2), "peak": round(ALU_PEAK_TFLOPS, 2),
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
                 "unit": "TFLOP/s", "frac": round(achieved / ALU_PEAK_TFLOPS, 4),
-                "flops_per_update": round(fpu, 2), "launch_ms": round(k_ms / n_kernels, 4),
-                "ms_per_10_mcs": round(k_ms, 4),
+                "flops_per_update": round(fpu, 2), "launch_ms": round(k_ms / n_res, 4),
+                "launches_per_10_mcs": n_kernels, "ms_per_10_mcs": round(k_ms, 4),
                 "updates_per_ns_kernel": round(upd / (k_ms * 1e6), 2),
                 "traffic": None, "tiling": tiling}
-        # DRAM bytes of both launches (one per L) of 10 MCS
+        # DRAM bytes of the resident launches of 10 MCS
         roof["traffic"] = NCU_TRAFFIC.get((kernel_source_hash(RESIDENT_SOURCES), wname, roof["kernel"]))
         return dict(value=value, ms_per_step=ms_max / steps, launches=launches, clocks=clocks,
                     roofline=roof, lat=None)
@@ -552,7 +561,7 @@ def main():
             r["lat"].destroy()
             bimodal[key] = {"value": round(r["value"], 3), "ms_per_step": round(r["ms_per_step"], 3),
                             "D": BIMODAL_D, "roofline": r["roofline"], "gpu_launches": r["launches"]}
-    small = None
+    small = mid = None
     if not args.no_small and not persistent:
         # many small lattices: resident steps against the streaming kernels,
         # and the sequential overrelaxation sweep, on the same inputs
@@ -571,6 +580,20 @@ def main():
                  "resident_over_streaming": round(res["value"] / strm["value"], 3),
                  "sequential_or_sweep": time_sequential_or(hsg, ws, inputs_s, torch)}
         del inputs_s
+        # mid-size lattices: parts of replica sets resident, PT between launches
+        wm = WORKLOADS[MID_WORKLOAD]
+        inputs_m = make_inputs(wm, rank)
+        res = run_form(hsg, torch, dist, MID_WORKLOAD, inputs_m, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
+                       persistent=True)
+        strm = run_form(hsg, torch, dist, MID_WORKLOAD, inputs_m, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak)
+        strm["lat"].destroy()
+        mid = {"workload": MID_WORKLOAD, "steps": k,
+               "resident": {"value": round(res["value"], 3), "ms_per_step": round(res["ms_per_step"], 3),
+                            "roofline": res["roofline"], "gpu_launches": res["launches"]},
+               "streaming_f16": {"value": round(strm["value"], 3), "ms_per_step": round(strm["ms_per_step"], 3),
+                                 "roofline": strm["roofline"]},
+               "resident_over_streaming": round(res["value"] / strm["value"], 3)}
+        del inputs_m
     e2e = None if args.no_e2e else e2e_run(hsg, torch, dist, w, inputs, args.steps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -610,6 +633,8 @@ def main():
             line["sequential_or_sweep"] = sequential
         if small is not None:
             line["small_lattices"] = small
+        if mid is not None:
+            line["mid_lattices"] = mid
         print(json.dumps(line), flush=True)
     dist.close()
     return 0
