@@ -1570,7 +1570,11 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
     HSG_CUDA(cudaMemcpyAsync(perm, h->d_perm, S * h->n_rep * h->NT * sizeof(int), cudaMemcpyDeviceToDevice,
                              h->stream));
     HSG_CUDA(cudaMemsetAsync(acc, 0, S * h->n_rep * acc_stride(h) * sizeof(long long), h->stream));
-    const int steps = (h->measure_every > 0 && h->measure_every <= kMaxStepsPerLaunch) ? h->measure_every : 10;
+    // as in the run: one step per launch when replica sets span several CTAs
+    const int steps = h->res_split ? 1
+                                   : (h->measure_every > 0 && h->measure_every <= kMaxStepsPerLaunch)
+                                         ? h->measure_every
+                                         : 10;
     PersistentParams p = persistent_params(h, b, steps);
     p.spins = sp;
     p.perm = perm;
