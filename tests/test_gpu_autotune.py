@@ -23,6 +23,8 @@ def _snapshot(lat):
     ([16], 4, False),
     # mixed: the small bucket may switch to two-pass while L = 64 stays fused
     ([16, 64], 4, False),
+    # resident steps on parts of replica sets (L = 16), PT between launches
+    ([16], 8, True),
 ])
 def test_autotune_keeps_state_and_trajectories(Ls, NT, persistent):
     betas = gi.linear_betas(0.3, 1.1, NT)
