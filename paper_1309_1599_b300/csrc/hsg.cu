@@ -22,6 +22,7 @@
 #include "persistent.cuh"
 #include "transfer.cuh"
 #include "sequential.cuh"
+#include "measure.cuh"
 #include "kernels.cuh"
 
 using namespace hsg;
@@ -639,13 +640,12 @@ hsg_status enqueue_measure(hsg_ctx* h, cudaStream_t st) {
     p.phase = b.d_phase;
     p.partial = b.d_mpart;
     const unsigned grid = static_cast<unsigned>(b.S_b * h->NT * b.P * b.m_chunks);
-    const size_t smem = 2 * sizeof(float) * b.L;
     *h->launch_sink += 2;
     const int n_units = b.S_b * h->NT * b.P;
     const unsigned wgrid = static_cast<unsigned>((n_units + kMeasureThreads / 32 - 1) / (kMeasureThreads / 32));
     dispatch(h->V, h->prec, [&](auto v, auto pr) {
       constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
-      if (b.m_warp) k_measure_warp<VV, P><<<wgrid, kMeasureThreads, smem, st>>>(p, n_units);
+      if (b.m_warp) k_measure_warp<VV, P><<<wgrid, kMeasureThreads, measure_block_smem(b.L), st>>>(p, n_units);
       else k_measure<VV, P><<<grid, kMeasureThreads, measure_block_smem(b.L), st>>>(p);
       return 0;
     });
@@ -892,14 +892,18 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     if (ps != HSG_OK) return bail(ps);
   }
   {
-    // the block measurement kernel keeps its accumulators in shared memory
+    // both measurement kernels keep their accumulators in shared memory
     size_t msmem = 0;
-    for (const Bucket& b : h->buckets)
-      if (!b.m_warp) msmem = std::max(msmem, measure_block_smem(b.L));
+    for (const Bucket& b : h->buckets) msmem = std::max(msmem, measure_block_smem(b.L));
     if (msmem > 0) {
       const cudaError_t e = dispatch(h->V, h->prec, [&](auto v, auto pr) {
-        return cudaFuncSetAttribute(k_measure<decltype(v)::value, decltype(pr)::value>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(msmem));
+        constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
+        const cudaError_t a = cudaFuncSetAttribute(k_measure<VV, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(msmem));
+        return a != cudaSuccess ? a
+                                : cudaFuncSetAttribute(k_measure_warp<VV, P>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       static_cast<int>(msmem));
       });
       if (e != cudaSuccess) {
         fail(HSG_ECUDA, std::string("measurement shared memory: ") + cudaGetErrorString(e));
