@@ -177,23 +177,36 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
   // cannot cancel, so the fast exponential serves both terms; expm1 is kept
   // for small kappa, where 1 - e^{-2 kappa} is small.  For y >= 1/2 the
   // argument of the logarithm lies in (0, 1/2], where the fast logarithm's
-  // relative error (about 2^-21) leaves w accurate to ~5e-7 relative; for
-  // y < 1/2, log1p keeps w accurate near the pole, where sin(theta) ~
-  // sqrt(2w) would amplify an absolute error.
+  // relative error (about 2^-21) leaves w accurate to ~5e-7 relative.  For
+  // y < 1/2 w must stay accurate near the pole, where sin(theta) ~ sqrt(2w)
+  // would amplify an absolute error: log1p for kappa <= 1/2, and for
+  // kappa > 1/2 a series below y = 1/16 and the fast logarithm above.
   float w;
   if (kappa < 1e-30f) {
     w = 2.0f * r0;
   } else {
-    float y, e2k;
+    float lg;
     if (kappa > 0.5f) {
-      e2k = __expf(-2.0f * kappa);
-      y = fmaf(-r0, e2k, r0);
+      const float e2k = __expf(-2.0f * kappa);
+      const float y = fmaf(-r0, e2k, r0);
+      // Without branches: one fast logarithm serves y >= 1/16, of 1 - y for
+      // y < 1/2 (1 - y rounds by at most 2^-25 there, and log(1 - y) <=
+      // -0.0645, so the logarithm's absolute error of 2^-21.4 leaves w
+      // within 8e-6 while sin(theta) >= 0.92) or of the sum above for
+      // y >= 1/2; below y = 1/16 the Mercator series of log(1 - y) to y^7
+      // is used (truncation error below 1e-9 relative).
+      const float arg = (y < 0.5f) ? 1.0f - y : fmaf(r0, e2k, 1.0f - r0);
+      const float lf = __logf(arg);
+      const float ps =
+          y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.0f / 7.0f, 1.0f / 6.0f), 0.2f), 0.25f),
+                                         1.0f / 3.0f), 0.5f), 1.0f);
+      lg = (y < 0.0625f) ? -ps : lf;
     } else {
       const float em = expm1f(-2.0f * kappa);
-      e2k = em + 1.0f;
-      y = -r0 * em;
+      const float e2k = em + 1.0f;
+      const float y = -r0 * em;
+      lg = (y < 0.5f) ? log1pf(-y) : __logf(fmaf(r0, e2k, 1.0f - r0));
     }
-    const float lg = (y < 0.5f) ? log1pf(-y) : __logf(fmaf(r0, e2k, 1.0f - r0));
     w = __fdividef(-lg, kappa);
   }
   w = fminf(fmaxf(w, 0.0f), 2.0f);
