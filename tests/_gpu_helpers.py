@@ -7,7 +7,7 @@ import oracle
 import paper_1309_1599_b300 as hsg
 
 SEED = 1
-# the benchmark spec tolerance: max |ds| per site after one sweep from identical input
+# parity tolerance: max |ds| per site after one sweep from identical input
 SWEEP_TOL = 2e-5
 # Heat-bath sites whose field direction lies within this distance of the
 # equator h_z = 0, where the azimuthal frame of the draw (Duff et al.) changes

@@ -9,9 +9,10 @@ therefore compared between ensembles of independent chains of the same
 Markov chain -- same couplings, independent initial spins and random streams
 -- with the pooled-variance two-sample t statistic; under the hypothesis
 that GPU and oracle sample the same process it is ~N(0,1) at any time,
-equilibrated or not.  Threshold: |t| < 3 per observable (north_star: "within
-3 sigma"), with a 4-sigma bound where many temperatures are compared at
-once, plus a bound on the mean of t^2.
+equilibrated or not.  Threshold: |t| < 3 per observable (the 3-sigma
+agreement the parity target asks of long-run averages), with a 4-sigma bound
+where many temperatures are compared at once, plus a bound on the mean of
+t^2.
 """
 import json
 import os
