@@ -82,10 +82,13 @@ def test_energies_match_oracle():
             assert abs(E[s, slot] - ref) <= 2e-6 * abs(ref)
 
 
-def test_resident_steps_equal_streaming_steps():
+@pytest.mark.parametrize("Ls", [[8, 12], [16]], ids=["whole_sets", "split_sets"])
+def test_resident_steps_equal_streaming_steps(Ls):
+    """Whole replica sets per CTA (L = 8, 12) and parts of sets with PT
+    between launches (L = 16, one-byte bonds resident beside one group)."""
     betas = gi.linear_betas(0.2, 0.8, 8)
-    a, _, _ = make_bimodal([8, 12], betas, 0.5, n_rep=2, layout=hsg.BATCHED, n_or=3, measure_every=2)
-    b, _, _ = make_bimodal([8, 12], betas, 0.5, n_rep=2, layout=hsg.BATCHED, n_or=3, measure_every=2,
+    a, _, _ = make_bimodal(Ls, betas, 0.5, n_rep=2, layout=hsg.BATCHED, n_or=3, measure_every=2)
+    b, _, _ = make_bimodal(Ls, betas, 0.5, n_rep=2, layout=hsg.BATCHED, n_or=3, measure_every=2,
                            persistent=True)
     a.run_steps(6)
     b.run_steps(6)
