@@ -1,0 +1,76 @@
+"""Seeded random configurations: the three ways of running a Monte Carlo step
+(fused one-pass sweeps, two-pass half-sweeps, shared-memory-resident steps)
+must give the same spins bit for bit, the same temperature labels and
+acceptances, and energies equal up to their summation order.  The draws
+cover mixed L, odd replica counts, one temperature, beta = 0, both layouts
+and all three coupling formats."""
+import numpy as np
+import pytest
+
+import hsg_inputs as gi
+import paper_1309_1599_b300 as hsg
+from _gpu_helpers import state
+
+pytestmark = pytest.mark.gpu
+
+
+def _config(seed):
+    rng = np.random.default_rng(1000 + seed)
+    layout = hsg.BATCHED if rng.random() < 0.6 else hsg.PLAIN
+    V = 2 if layout == hsg.BATCHED else 1
+    n_L = int(rng.integers(1, 3))
+    Ls = sorted({int(x) for x in rng.choice([4, 6, 8, 10, 12, 16], size=n_L)}, reverse=bool(rng.random() < 0.5))
+    NT = int(rng.choice([1, 2, 3, 4, 6, 8]))
+    if V == 2 and NT % 2:
+        NT += 1
+    n_rep = int(rng.integers(1, 4))
+    if V == 2 and (NT * n_rep) % 2:
+        n_rep += 1
+    betas = np.sort(rng.uniform(0.0, 3.0, NT))
+    if rng.random() < 0.3:
+        betas[0] = 0.0
+    betas = np.unique(betas)
+    NT = len(betas)
+    if V == 2 and NT % 2:
+        betas = np.append(betas, betas[-1] + 0.5)
+    prec = [hsg.F32, hsg.F16, hsg.BIMODAL][int(rng.integers(0, 3))]
+    n_or = int(rng.integers(0, 4))
+    me = int(rng.integers(0, 3))
+    return dict(Ls=Ls, betas=list(betas), n_rep=n_rep, layout=layout, prec=prec, n_or=n_or, me=me)
+
+
+def _make(c, **kw):
+    lat = hsg.Lattice(c["Ls"], c["betas"], n_replicas=c["n_rep"], coupling_prec=c["prec"], layout=c["layout"],
+                      n_or=c["n_or"], measure_every=c["me"], seed=7, bimodal_D=0.6, **kw)
+    for s, L in enumerate(c["Ls"]):
+        if c["prec"] == hsg.BIMODAL:
+            lat.set_couplings_bimodal(s, gi.bimodal_bits(L, 7, s))
+        else:
+            lat.set_couplings(s, gi.couplings(L, 7, s, precision="f16" if c["prec"] == hsg.F16 else "f32"))
+        lat.set_spins_sample(s, gi.random_spins_batch(L, 7, s, lat.R))
+    return lat
+
+
+def _result(lat, steps):
+    lat.run_steps(steps)
+    return state(lat), lat.get_perm().copy(), lat.get_pt_accepts().copy(), lat.get_energies().copy()
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_random_configurations_agree_across_step_kernels(seed):
+    c = _config(seed)
+    steps = 4
+    runs = {"fused": _result(_make(c), steps),
+            "two_pass": _result(_make(c, sweep_kernel=hsg.SWEEP_TWO_PASS), steps)}
+    try:
+        res = _make(c, persistent=True)
+    except hsg.HsgError:
+        res = None                          # a lattice group too large for shared memory
+    if res is not None:
+        runs["resident"] = _result(res, steps)
+    ref = runs["fused"]
+    for name, r in runs.items():
+        assert all(np.array_equal(x, y) for rx, ry in zip(ref[0], r[0]) for x, y in zip(rx, ry)), (name, c)
+        assert np.array_equal(ref[1], r[1]), (name, c)
+        assert np.array_equal(ref[2], r[2]), (name, c)
+        assert np.allclose(ref[3], r[3], rtol=1e-9, atol=1e-9 * max(1.0, np.abs(ref[3]).max())), (name, c)
