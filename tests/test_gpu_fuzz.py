@@ -1,5 +1,6 @@
-"""Seeded random configurations: the three ways of running a Monte Carlo step
-(fused one-pass sweeps, two-pass half-sweeps, shared-memory-resident steps)
+"""Seeded random configurations: the ways of running a Monte Carlo step
+(fused one-pass sweeps, two-pass half-sweeps, shared-memory-resident steps,
+and whatever shapes the autotuner picks)
 must give the same spins bit for bit, the same temperature labels and
 acceptances, and energies equal up to their summation order.  The draws
 cover mixed L, odd replica counts, one temperature, beta = 0, both layouts
@@ -60,8 +61,11 @@ def _result(lat, steps):
 def test_random_configurations_agree_across_step_kernels(seed):
     c = _config(seed)
     steps = 4
+    tuned = _make(c)
+    tuned.autotune()                        # may change band heights or leave the fused sweep
     runs = {"fused": _result(_make(c), steps),
-            "two_pass": _result(_make(c, sweep_kernel=hsg.SWEEP_TWO_PASS), steps)}
+            "two_pass": _result(_make(c, sweep_kernel=hsg.SWEEP_TWO_PASS), steps),
+            "autotuned": _result(tuned, steps)}
     try:
         res = _make(c, persistent=True)
     except hsg.HsgError:
