@@ -58,10 +58,9 @@ typedef enum {
   HSG_EIO = 6       /* checkpoint file could not be read or written */
 } hsg_status;
 
-/* Storage precision of the couplings on the device.  Values are rounded once
- * (round to nearest even) from the float32 host array. */
-/* Coupling storage: FP32, FP16, or bimodal (Sec. II.A: J = +-1 and
- * D^ab = +-D, one byte per bond holding the seven signs). */
+/* Storage precision of the couplings on the device: FP32 or FP16, rounded
+ * once (to nearest even) from the float32 host array, or bimodal (Sec. II.A:
+ * J = +-1 and D^ab = +-D, one byte per bond holding the seven signs). */
 enum { HSG_F32 = 0, HSG_F16 = 1, HSG_BIMODAL = 2 };
 
 /* Device spin layout.
@@ -77,7 +76,8 @@ enum { HSG_LAYOUT_PLAIN = 0, HSG_LAYOUT_BATCHED = 1 };
  *                       and written once, planes staged in shared memory),
  *                       wherever the lattice size allows it (whole planes, or
  *                       bands of at least 8 rows that divide L); the two-pass
- *                       kernel otherwise.  Doubles the spin memory.
+ *                       kernel otherwise, or where hsg_autotune finds it
+ *                       faster.  Doubles the spin memory.
  *   HSG_SWEEP_TWO_PASS  always one kernel per colour half-sweep.
  * Both give the same spins bit for bit. */
 enum { HSG_SWEEP_AUTO = 0, HSG_SWEEP_TWO_PASS = 1 };
@@ -169,9 +169,10 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float *s_out);
 
 /* Every lattice slot of one sample at once, host float32 [R][N][3] (slots
  * 0 .. R-1, each [N][3] in natural site order), staged in chunks of at most
- * 256 MiB instead of R calls.  Synchronous like the one-slot calls; the pointer may be pinned or
- * pageable.  HSG_EINVAL on a NULL argument or a bad sample (nothing stored);
- * HSG_ENOMEM if the staging buffer cannot be allocated. */
+ * 256 MiB instead of R calls.  Synchronous like the one-slot calls; the
+ * pointer may be pinned or pageable.  HSG_EINVAL on a NULL argument or a bad
+ * sample (nothing stored); HSG_ENOMEM if the staging buffer cannot be
+ * allocated. */
 hsg_status hsg_set_spins_sample(hsg_t h, int sample, const float *s);
 hsg_status hsg_get_spins_sample(hsg_t h, int sample, float *s_out);
 
@@ -232,7 +233,8 @@ hsg_status hsg_measure(hsg_t h);
 /* n_steps Monte Carlo steps (Sec. III): one heat-bath sweep, n_or
  * overrelaxation sweeps, the energies, one PT sweep when N_T > 1, and a
  * measurement after every measure_every-th step (counted over the life of
- * the context).  Replayed from captured CUDA graphs. */
+ * the context).  Streaming contexts replay captured CUDA graphs; persistent
+ * ones launch the shared-memory-resident steps (see hsg_config). */
 hsg_status hsg_run_steps(hsg_t h, int n_steps);
 
 /* Accumulated observables, double [S][N_T][HSG_NOBS], and the number of
