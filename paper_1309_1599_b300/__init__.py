@@ -132,6 +132,34 @@ def _ptr(a) -> ctypes.c_void_p:
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def _host_f32(a, n: int, out: bool = False):
+    """A contiguous float32 host buffer of n elements: a numpy array, or a
+    CPU torch tensor (pinned or not).  Inputs are converted when they are
+    numpy-like; output buffers must already have the right type and size.
+    Raises ValueError otherwise, so that no call reads or writes past a
+    caller's buffer."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.device.type != "cpu" or a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"expected a contiguous float32 CPU tensor of {n} elements")
+        return a
+    if out:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous and a.size == n):
+            raise ValueError(f"expected a C-contiguous float32 numpy array of {n} elements")
+        return a
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} elements, got {a.size}")
+    return a
+
+
+def _device_f32(t, n: int) -> None:
+    """Checks a contiguous float32 CUDA tensor of n elements (ValueError)."""
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"expected a contiguous float32 CUDA tensor of {n} elements")
+
+
 def _require_gpu() -> None:
     import torch
     if not torch.cuda.is_available():
@@ -223,11 +251,7 @@ class Lattice:
     def set_couplings(self, sample: int, J6) -> None:
         """Couplings float32 [N, 3, 6] from a numpy array or a contiguous CPU
         torch tensor (pinned or not)."""
-        if hasattr(J6, "data_ptr"):
-            assert J6.is_contiguous() and J6.numel() == self.N(sample) * 18
-        else:
-            J6 = np.ascontiguousarray(J6, dtype=np.float32)
-            assert J6.size == self.N(sample) * 18
+        J6 = _host_f32(J6, self.N(sample) * 18)
         _check(self._lib.hsg_set_couplings(self._h, sample, _ptr(J6)))
 
     def get_couplings(self, sample: int) -> np.ndarray:
@@ -237,7 +261,8 @@ class Lattice:
 
     def set_couplings_bimodal(self, sample: int, bits) -> None:
         bits = np.ascontiguousarray(bits, dtype=np.uint8)
-        assert bits.size == self.N(sample) * 3
+        if bits.size != self.N(sample) * 3:
+            raise ValueError(f"expected {self.N(sample) * 3} bond bytes, got {bits.size}")
         _check(self._lib.hsg_set_couplings_bimodal(self._h, sample, _ptr(bits)))
 
     def get_couplings_bimodal(self, sample: int) -> np.ndarray:
@@ -246,36 +271,27 @@ class Lattice:
         return out
 
     def set_spins(self, sample: int, slot: int, s) -> None:
-        if hasattr(s, "data_ptr"):
-            assert s.is_contiguous() and s.numel() == self.N(sample) * 3
-        else:
-            s = np.ascontiguousarray(s, dtype=np.float32)
-            assert s.size == self.N(sample) * 3
+        s = _host_f32(s, self.N(sample) * 3)
         _check(self._lib.hsg_set_spins(self._h, sample, slot, _ptr(s)))
 
     def get_spins(self, sample: int, slot: int, out=None):
         if out is None:
             out = np.empty((self.N(sample), 3), dtype=np.float32)
+        out = _host_f32(out, self.N(sample) * 3, out=True)
         _check(self._lib.hsg_get_spins(self._h, sample, slot, _ptr(out)))
         return out
 
     def set_spins_sample(self, sample: int, s) -> None:
         """Every lattice slot of a sample from host float32 [R, N, 3] (a numpy
         array or a contiguous CPU torch tensor, pinned or not)."""
-        if hasattr(s, "data_ptr"):
-            assert s.is_contiguous() and s.numel() == self.R * self.N(sample) * 3
-        else:
-            s = np.ascontiguousarray(s, dtype=np.float32)
-            assert s.size == self.R * self.N(sample) * 3
+        s = _host_f32(s, self.R * self.N(sample) * 3)
         _check(self._lib.hsg_set_spins_sample(self._h, sample, _ptr(s)))
 
     def get_spins_sample(self, sample: int, out=None):
         """Every lattice slot of a sample as host float32 [R, N, 3]."""
         if out is None:
             out = np.empty((self.R, self.N(sample), 3), dtype=np.float32)
-        else:
-            assert out.is_contiguous() if hasattr(out, "data_ptr") else out.flags.c_contiguous
-            assert (out.numel() if hasattr(out, "data_ptr") else out.size) == self.R * self.N(sample) * 3
+        out = _host_f32(out, self.R * self.N(sample) * 3, out=True)
         _check(self._lib.hsg_get_spins_sample(self._h, sample, _ptr(out)))
         return out
 
@@ -283,14 +299,12 @@ class Lattice:
     def set_spins_device(self, sample: int, slot: int, tensor) -> None:
         """From a contiguous float32 CUDA tensor [N, 3] on the context's device
         (stream-ordered, no host copy)."""
-        assert tensor.is_cuda and tensor.dtype.itemsize == 4 and tensor.is_contiguous()
-        assert tensor.numel() == self.N(sample) * 3
+        _device_f32(tensor, self.N(sample) * 3)
         _check(self._lib.hsg_set_spins_device(self._h, sample, slot, ctypes.c_void_p(tensor.data_ptr())))
 
     def get_spins_device(self, sample: int, slot: int, tensor) -> None:
         """Into a contiguous float32 CUDA tensor [N, 3] (stream-ordered)."""
-        assert tensor.is_cuda and tensor.dtype.itemsize == 4 and tensor.is_contiguous()
-        assert tensor.numel() == self.N(sample) * 3
+        _device_f32(tensor, self.N(sample) * 3)
         _check(self._lib.hsg_get_spins_device(self._h, sample, slot, ctypes.c_void_p(tensor.data_ptr())))
 
     def sweep_hb(self, n: int = 1) -> None:
@@ -312,7 +326,8 @@ class Lattice:
 
     def set_energies(self, E) -> None:
         E = np.ascontiguousarray(E, dtype=np.float64)
-        assert E.size == self.S * self.R
+        if E.size != self.S * self.R:
+            raise ValueError(f"expected {self.S * self.R} energies, got {E.size}")
         _check(self._lib.hsg_set_energies(self._h, _ptr(E)))
 
     def pt_swap(self) -> None:
@@ -325,7 +340,8 @@ class Lattice:
 
     def set_perm(self, perm) -> None:
         perm = np.ascontiguousarray(perm, dtype=np.int32)
-        assert perm.size == self.S * self.n_replicas * self.NT
+        if perm.size != self.S * self.n_replicas * self.NT:
+            raise ValueError(f"expected {self.S * self.n_replicas * self.NT} labels, got {perm.size}")
         _check(self._lib.hsg_set_perm(self._h, _ptr(perm)))
 
     def get_pt_accepts(self) -> np.ndarray:

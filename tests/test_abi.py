@@ -100,3 +100,21 @@ def test_binding_refuses_without_gpu():
         pytest.skip("a GPU is visible")
     with pytest.raises(RuntimeError, match="CUDA device"):
         hsg.Lattice(8, [1.0])
+
+
+def test_binding_checks_host_buffers():
+    """Buffers of the wrong size, type or device are refused before any call
+    reaches the library (no read or write past a caller's buffer)."""
+    import torch
+    f = hsg._host_f32
+    assert f([[1.0, 2.0, 3.0]], 3).dtype == np.float32
+    with pytest.raises(ValueError):
+        f(np.zeros(5, np.float32), 6)
+    with pytest.raises(ValueError):
+        f(np.zeros(6, np.float64), 6, out=True)          # an output must already be float32
+    with pytest.raises(ValueError):
+        f(np.zeros((6, 2), np.float32)[:, 0], 6, out=True)  # not contiguous
+    with pytest.raises(ValueError):
+        f(torch.zeros(6, dtype=torch.float64), 6)
+    t = torch.zeros(6, dtype=torch.float32)
+    assert f(t, 6) is t
