@@ -78,3 +78,32 @@ def test_random_configurations_agree_across_step_kernels(seed):
         assert np.array_equal(ref[1], r[1]), (name, c)
         assert np.array_equal(ref[2], r[2]), (name, c)
         assert np.allclose(ref[3], r[3], rtol=1e-9, atol=1e-9 * max(1.0, np.abs(ref[3]).max())), (name, c)
+
+
+def _bands(L):
+    """Band heights the fused sweep accepts at L (divisors >= 8, and whole
+    planes when L*L/2 threads fit in a block)."""
+    out = [B for B in range(8, L) if L % B == 0 and (B + 2) * (L // 2) <= 576]
+    if L * (L // 2) <= 576:
+        out.append(L)
+    return out
+
+
+TILINGS = [(L, B) for L in (16, 20, 24, 28, 32, 40, 48, 56, 64) for B in _bands(L)]
+
+
+@pytest.mark.parametrize("L,band", TILINGS, ids=[f"L{L}_b{B}" for L, B in TILINGS])
+def test_every_fused_tiling_equals_the_two_pass_sweep(L, band):
+    """Each band height the fused sweep accepts, including the compile-time
+    specialisations (L = 32 and 64 in 8-row bands), gives the two-pass
+    kernel's spins bit for bit over heat-bath and overrelaxation sweeps."""
+    c = dict(Ls=[L], betas=[0.7, 1.9], n_rep=1, layout=hsg.BATCHED, prec=hsg.F16, n_or=2, me=0)
+    a = _make(c, band_rows=band)
+    plan = a.get_sweep_plan(0)
+    assert plan["fused"] and plan["band_rows"] == band
+    b = _make(c, sweep_kernel=hsg.SWEEP_TWO_PASS)
+    ra, rb = _result(a, 2), _result(b, 2)
+    assert all(np.array_equal(x, y) for rx, ry in zip(ra[0], rb[0]) for x, y in zip(rx, ry))
+    assert np.array_equal(ra[1], rb[1])
+    a.destroy()
+    b.destroy()
