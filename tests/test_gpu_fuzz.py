@@ -107,3 +107,26 @@ def test_every_fused_tiling_equals_the_two_pass_sweep(L, band):
     assert np.array_equal(ra[1], rb[1])
     a.destroy()
     b.destroy()
+
+
+RESIDENT = [(L, layout, NT) for L in (4, 6, 8, 10, 12, 14, 16, 18, 20)
+            for layout in (hsg.PLAIN, hsg.BATCHED) for NT in (2, 16)]
+
+
+@pytest.mark.parametrize("L,layout,NT", RESIDENT,
+                         ids=[f"L{L}_{'B' if lay else 'P'}_T{NT}" for L, lay, NT in RESIDENT])
+def test_resident_steps_equal_streaming_steps_at_every_size(L, layout, NT):
+    """Resident steps at every even L up to 20, one and two lattices per
+    element, with replica sets that fit one CTA (N_T = 2) and, from L = 8
+    or 10 on, sets split over several CTAs (N_T = 16), against the streaming
+    path: same spins, labels and acceptances."""
+    c = dict(Ls=[L], betas=list(gi.linear_betas(0.3, 1.5, NT)), n_rep=2, layout=layout, prec=hsg.F16,
+             n_or=2, me=0)
+    a = _make(c)
+    b = _make(c, persistent=True)
+    ra, rb = _result(a, 3), _result(b, 3)
+    assert all(np.array_equal(x, y) for rx, ry in zip(ra[0], rb[0]) for x, y in zip(rx, ry))
+    assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[2], rb[2])
+    assert np.allclose(ra[3], rb[3], rtol=1e-9, atol=1e-9 * max(1.0, np.abs(ra[3]).max()))
+    a.destroy()
+    b.destroy()
