@@ -190,11 +190,11 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
       const float e2k = __expf(-2.0f * kappa);
       const float y = fmaf(-r0, e2k, r0);
       // Without branches: one fast logarithm serves y >= 1/16, of 1 - y for
-      // y < 1/2 (1 - y rounds by at most 2^-25 there, and log(1 - y) <=
-      // -0.0645, so the logarithm's absolute error of 2^-21.4 leaves w
-      // within 8e-6 while sin(theta) >= 0.92) or of the sum above for
-      // y >= 1/2; below y = 1/16 the Mercator series of log(1 - y) to y^7
-      // is used (truncation error below 1e-9 relative).
+      // y < 1/2 (1 - y rounds by at most 2^-25 there, and the logarithm's
+      // absolute error of 2^-21.4 leaves w within 7.2e-7 for kappa > 1/2,
+      // while sin(theta) >= 0.92) or of the sum above for y >= 1/2; below
+      // y = 1/16 the Mercator series of log(1 - y) to y^7 is used
+      // (truncation error below 1e-9 relative).
       const float arg = (y < 0.5f) ? 1.0f - y : fmaf(r0, e2k, 1.0f - r0);
       const float lf = __logf(arg);
       const float ps =
@@ -210,8 +210,20 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
     w = __fdividef(-lg, kappa);
   }
   w = fminf(fmaxf(w, 0.0f), 2.0f);
+  // 1 + u = 2 - w.  Near the antipole (u -> -1) it is small and cancels in
+  // 2 - w, which sin(theta) = sqrt(w (2 - w)) would magnify; for w > 1.99
+  // (sin(theta) < 0.14) it is evaluated directly as 2 - w = log1p((1 - r0)
+  // (e^{2 kappa} - 1)) / kappa, with 1 - r0 exact.  There (1 - r0)
+  // (e^{2 kappa} - 1) < e^{0.01 kappa} - 1 stays below 1/2, and w > 1.99 needs
+  // 1 - r0 < e^{-1.99 kappa}, so kappa < 8.4 (1 - r0 >= 2^-24) and
+  // e^{2 kappa} is finite; the kappa bound below is a second guard.
+  float wc = 2.0f - w;
+  if (w > 1.99f && kappa >= 1e-30f && kappa < 40.0f) {
+    wc = __fdividef(log1pf((1.0f - r0) * expm1f(2.0f * kappa)), kappa);
+    w = 2.0f - wc;
+  }
   const float u = 1.0f - w;
-  const float w2 = fmaxf(w * (2.0f - w), 0.0f);
+  const float w2 = fmaxf(w * wc, 0.0f);
   const float st = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;   // sin(theta), 2 ulp
   // azimuth phi = 2 pi r1: evaluated as phi - pi in (-pi, pi), where the
   // fast sine and cosine are accurate to 2^-21.4, then reflected

@@ -331,3 +331,24 @@ def test_device_pointer_spins_roundtrip():
                 lat.get_spins_device(s, slot, out)
                 torch.cuda.synchronize()
                 assert np.array_equal(out.cpu().numpy(), host)
+
+
+SIZES = [(L, prec, layout) for L in (4, 6, 10, 14, 18, 20) for prec in (hsg.F32, hsg.F16)
+         for layout in (hsg.PLAIN, hsg.BATCHED)]
+
+
+@pytest.mark.parametrize("L,prec,layout", SIZES,
+                         ids=[f"L{L}_{'f16' if p else 'f32'}_{'B' if lay else 'P'}" for L, p, lay in SIZES])
+def test_per_half_sweep_parity_across_sizes(L, prec, layout):
+    """One heat-bath and two overrelaxation sweeps per half-sweep against the
+    oracle at lattice sizes the other cases do not use (whole-plane and
+    banded fused tilings), both coupling precisions and both layouts."""
+    lat, J = make([L], [0.6, 2.2], n_rep=2, prec=prec, layout=layout)
+    for kind in (oracle.HB, oracle.OR, oracle.OR):
+        hb_t = int(lat.get_counters()[0])
+        before = state(lat)
+        (lat.sweep_hb if kind == oracle.HB else lat.sweep_or)(1)
+        d, amb, du = compare_sweep(lat, J, before, state(lat), kind, hb_t)
+        assert d <= SWEEP_TOL and du <= SWEEP_TOL, (kind, d, du)
+        assert amb <= max(3, 1e-3 * lat.R * L ** 3)
+    lat.destroy()
