@@ -6,7 +6,7 @@ sweep, observables every 10 steps).  Chain c starts from the random spins of
 generator sample c and uses the random streams of sample index c, as chain c
 of the GPU test does.  Calls only the oracle and the seeded input generator.
 
-    python tests/golden/make_pt_L16_oracle.py      # 4 chains in parallel
+    python tests/golden/make_pt_L16_oracle.py      # 8 chains in parallel
 """
 import json
 import multiprocessing as mp
@@ -17,7 +17,7 @@ import time
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-L, N_T, N_REP, SEED, N_CHAINS = 16, 16, 2, 1, 4
+L, N_T, N_REP, SEED, N_CHAINS = 16, 16, 2, 1, 8
 STEPS, BLOCK, MEASURE_EVERY, N_OR = 20000, 1000, 10, 8
 
 

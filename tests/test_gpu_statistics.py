@@ -90,7 +90,7 @@ def test_parallel_tempering_L16_matches_stored_oracle():
     """L=16, the couplings of sample 0, 16 temperatures evenly spaced in
     [0.15, 0.75] x 2 replicas, 20000 steps of HB + 8 OR + PT, observables
     every 10 steps.  Averages over the second half of 16 GPU chains against
-    the 4 oracle chains stored by tests/golden/make_pt_L16_oracle.py, for
+    the 8 oracle chains stored by tests/golden/make_pt_L16_oracle.py, for
     e, q2, q2(k_min) and q2_CG at every temperature (64 statistics): all
     |t| < 4 and mean t^2 < 2; the energies |t| < 3."""
     with open(os.path.join(HERE, "golden", "pt_L16_oracle.json")) as f:
