@@ -69,6 +69,8 @@ RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
     # profiles/k_sweep_fused_or_L64_S1_R64_f16.md: 387.3 MB for one sample, x8 samples
     ("69c3411320c0911f", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3098695680,
+    # profiles/k_sweep_fused_or_L32_S64_R48_f16.md: one launch of the bench's workload
+    ("69c3411320c0911f", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645407744,
     # profiles/k_persistent_L8x256_L12x256_R32_f16.md: both launches of 10 MCS
     ("208dcb75e54b7286", "L8x256_L12x256_R32_f16",
      "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 356347136,
@@ -245,8 +247,7 @@ def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_ro
             lat.set_couplings_bimodal(s, gi.bimodal_bits(Ls[s], seed, samples[s]))
         else:
             lat.set_couplings(s, J[s])
-        for j in range(lat.R):
-            lat.set_spins(s, j, spins[s][j])
+        lat.set_spins_sample(s, np.stack(spins[s]))
     if band_rows == 0:
         lat.autotune()                 # launch shapes timed on this data, outside any timed region
     return lat
