@@ -161,10 +161,12 @@ class Dist:
 # ----------------------------------------------------------------------------
 # inputs
 # ----------------------------------------------------------------------------
-def make_inputs(w, rank, seed=1):
+def make_inputs(w, rank, seed=1, n_samples=None):
+    """Seeded inputs of this rank's samples (the first n_samples of them if
+    given)."""
     import hsg_inputs as gi
     Ls, S, R = sample_Ls(w), w["S"], w["n_rep"] * w["NT"]
-    samples = [rank * S + s for s in range(S)]
+    samples = [rank * S + s for s in range(S if n_samples is None else min(S, n_samples))]
     J = [gi.couplings(Ls[s], seed, sg, precision="f16") for s, sg in enumerate(samples)]
     spins = [[gi.random_spins(Ls[s], seed, sg, j) for j in range(R)] for s, sg in enumerate(samples)]
     beta = gi.linear_betas(w["Tmin"], w["Tmax"], w["NT"])
@@ -481,10 +483,27 @@ def cpu_baseline(w, inputs, budget_s=15.0):
                       f"{dt:.1f} s"}
 
 
+def workload_config(name, w, world):
+    """The `config` object of the JSON line: the workload and its shape."""
+    persistent = w.get("persistent", False)
+    return {"workload": name,
+            "L": w["L"] if "L" in w else sorted(set(sample_Ls(w))),
+            "samples_per_gpu": w["S"],
+            "lattices_per_sample": w["n_rep"] * w["NT"], "n_temps": w["NT"],
+            "T_range": [w["Tmin"], w["Tmax"]], "n_or": w["n_or"],
+            "couplings": "gaussian, FP16-quantised", "layout": "batched",
+            "step": f"{MCS_PER_STEP} MCS (HB + {w['n_or']} OR + PT each) + 1 measurement",
+            "l2": ("no flush: spins per GPU exceed L2 (126 MB)" if not persistent else
+                   "no flush: spins stay in shared memory within a launch; "
+                   "the whole set (220 MB per GPU) exceeds L2"),
+            "resident": persistent,
+            "parallelism": f"replicas x{world} (independent samples per GPU)"}
+
+
 def reference_arm(args, w, world, rank, local):
     if rank != 0:
         return 0
-    inputs = make_inputs(w, 0)
+    inputs = make_inputs(w, 0, n_samples=1)
     threads = os.cpu_count() or 1
     times, ups = [], 0
     for i in range(args.warmup + args.steps):
@@ -498,10 +517,10 @@ def reference_arm(args, w, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "step": "1 MCS of 1 sample (bounded CPU sample)"},
+            "config": workload_config(args.workload, w, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
                              "sample": f"each step: 1 MCS of sample 0 ({w['n_rep'] * w['NT']} lattices "
-                                       f"of L={sample_Ls(w)[0]})"},
+                                       f"of L={sample_Ls(w)[0]}), a bounded sample of the workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -604,18 +623,7 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(batched["ms_per_step"], 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload,
-                           "L": w["L"] if "L" in w else sorted(set(sample_Ls(w))),
-                           "samples_per_gpu": w["S"],
-                           "lattices_per_sample": w["n_rep"] * w["NT"], "n_temps": w["NT"],
-                           "T_range": [w["Tmin"], w["Tmax"]], "n_or": w["n_or"],
-                           "couplings": "gaussian, FP16-quantised", "layout": "batched",
-                           "step": f"{MCS_PER_STEP} MCS (HB + {w['n_or']} OR + PT each) + 1 measurement",
-                           "l2": ("no flush: spins per GPU exceed L2 (126 MB)" if not persistent else
-                                  "no flush: spins stay in shared memory within a launch; "
-                                  "the whole set (220 MB per GPU) exceeds L2"),
-                           "resident": persistent,
-                           "parallelism": f"replicas x{world} (independent samples per GPU)"},
+                "config": workload_config(args.workload, w, world),
                 "roofline": batched["roofline"], "gpu_launches": batched["launches"],
                 "clocks": batched["clocks"], "e2e": e2e, "cpu_baseline": cpu}
         if plain is not None:
