@@ -416,8 +416,9 @@ def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampl
 
 def e2e_run(hsg, torch, dist, w, inputs, steps):
     """Whole job through the public API from pinned host buffers: couplings and
-    initial spins host->device, `steps` bench steps, observables and final
-    spins device->host.  Wall time around it, synchronised."""
+    initial spins host->device, `steps` bench steps each followed by a read of
+    the observables (the step's result) to the host, and the final spins
+    device->host.  Wall time around it, synchronised."""
     samples, J, spins, beta = inputs
     Ls, S = sample_Ls(w), len(samples)
     lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
@@ -438,7 +439,7 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
         lat.set_spins_sample(s, s_h[s])
     for _ in range(steps):
         lat.run_steps(MCS_PER_STEP)
-    obs, counts = lat.read_observables()
+        obs, counts = lat.read_observables()
     for s in range(S):
         lat.get_spins_sample(s, out=out_h[s])
     torch.cuda.synchronize()
@@ -446,7 +447,7 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     lat.destroy()
     updates = R * n_sites * (1 + w["n_or"]) * MCS_PER_STEP * steps * dist.world
     h2d = sum(x.numel() * 4 for x in J_h) + R * n_sites * 12
-    d2h = obs.nbytes + counts.nbytes + R * n_sites * 12
+    d2h = (obs.nbytes + counts.nbytes) * steps + R * n_sites * 12
     return {"value": updates / (dt * 1e9), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
             "wall_s": round(dt, 3)}
