@@ -119,13 +119,24 @@ def test_parallel_tempering_L16_matches_stored_oracle():
     assert np.all(np.abs(z_sd) < 4), z_sd
 
 
-def test_full_size_throughput_workload_sampled_parity():
-    """The launch configuration bench.py times (L=64, 8 samples x 64
-    lattices, FP16 couplings, two lattices per element, fused sweep in bands
-    of 8 rows): one heat-bath and one overrelaxation sweep from the initial
-    state, checked per half-sweep on whole sampled lattices, plus the fused
-    energies and one PT sweep against the oracle."""
-    L, S, NT, n_rep, seed = 64, 8, 32, 2, 1
+# the two streaming workloads bench.py times: L, samples, temperatures, and
+# the (sample, slot) pairs checked against the oracle
+FULL_SIZE = {
+    "L64_S8_R64": (64, 8, 32, [(0, 0), (0, 1), (0, 63), (3, 20), (7, 62), (7, 63)]),
+    "L32_S64_R48": (32, 64, 24, [(0, 0), (0, 1), (0, 47), (31, 20), (63, 46), (63, 47)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FULL_SIZE))
+def test_full_size_throughput_workload_sampled_parity(name):
+    """The launch configurations bench.py times (L=64, 8 samples x 64
+    lattices, the default, and L=32, 64 samples x 48 lattices; FP16
+    couplings, two lattices per element, fused sweep in bands of 8 rows): one
+    heat-bath and one overrelaxation sweep from the initial state, checked per
+    half-sweep on whole sampled lattices, plus the fused energies and one PT
+    sweep of every replica set against the oracle."""
+    L, S, NT, sampled = FULL_SIZE[name]
+    n_rep, seed = 2, 1
     beta = gi.linear_betas(0.15, 0.75, NT)
     lat = hsg.Lattice([L] * S, beta, n_replicas=n_rep, coupling_prec=hsg.F16, layout=hsg.BATCHED,
                       n_or=8, measure_every=10, seed=seed)
@@ -134,9 +145,7 @@ def test_full_size_throughput_workload_sampled_parity():
     J = [gi.couplings(L, seed, s, precision="f16") for s in range(S)]
     for s in range(S):
         lat.set_couplings(s, J[s])
-        for j in range(lat.R):
-            lat.set_spins(s, j, gi.random_spins(L, seed, s, j))
-    sampled = [(0, 0), (0, 1), (0, 63), (3, 20), (7, 62), (7, 63)]
+        lat.set_spins_sample(s, np.stack([gi.random_spins(L, seed, s, j) for j in range(lat.R)]))
 
     for kind in (oracle.HB, oracle.OR):
         hb_t = int(lat.get_counters()[0])
@@ -157,7 +166,10 @@ def test_full_size_throughput_workload_sampled_parity():
                 # frame-ambiguous sites (field at the equator h_z = 0) excepted
                 h = oracle.fields(L, J9, before[(s, slot)], 0) + oracle.fields(L, J9, mixed, 1)
                 amb = np.abs(h[:, 2]) < 1e-4 * np.linalg.norm(h, axis=1)
-                assert amb.mean() < 3e-4          # expected fraction 1e-4
+                # isotropic field directions put a fraction 1e-4 there: a
+                # Poisson count, bounded 6 sigma (+6) above its mean
+                lam = 1e-4 * amb.size
+                assert amb.sum() <= lam + 6 * np.sqrt(lam) + 6, amb.sum()
                 diff = diff[~amb]
             assert diff.max() <= SWEEP_TOL, ((s, slot), kind, diff.max())
     # energies fused into that overrelaxation sweep, and one PT sweep
