@@ -84,3 +84,43 @@ def test_persistent_step_matches_oracle_step_from_equilibrium():
     for j in range(lat.R):
         ref = oracle.energy(8, oracle.j9_from_j6(J[0]), lat.get_spins(0, j).astype(np.float64))
         assert abs(E[j] - ref) <= 2e-6 * abs(ref)
+
+
+def test_bench_small_lattice_workload_resident_equals_streaming():
+    """The mixed small-lattice workload at the size and launch configuration
+    bench.py times (256 samples of L=8 and 256 of L=12, 4 replicas x 8
+    temperatures, FP16 couplings, two lattices per element, shapes chosen by
+    the autotuner): one bench step of 10 MCS with resident launches equals
+    the streaming kernels on every lattice bit for bit, with the same labels,
+    acceptances and counters, and energies and observables equal up to their
+    summation order."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    name = "L8x256_L12x256_R32_f16"
+    w = bench.WORKLOADS[name]
+    samples, J, spins, beta = bench.make_inputs(w, 0)
+    lats = [bench.build_lattice(hsg, w, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=p)
+            for p in (False, True)]
+    del spins
+    launches = []
+    for lat in lats:
+        l0 = lat.get_launch_count()
+        lat.run_steps(bench.MCS_PER_STEP)
+        launches.append(lat.get_launch_count() - l0)
+    a, b = lats
+    assert launches[1] < launches[0], launches
+    for s in range(a.S):
+        assert np.array_equal(a.get_spins_sample(s), b.get_spins_sample(s)), s
+    assert np.array_equal(a.get_perm(), b.get_perm())
+    assert np.array_equal(a.get_pt_accepts(), b.get_pt_accepts())
+    assert np.array_equal(a.get_counters(), b.get_counters())
+    Ea, Eb = a.get_energies(), b.get_energies()
+    assert np.allclose(Ea, Eb, rtol=1e-9, atol=1e-9 * np.abs(Ea).max())
+    oa, ca = a.read_observables()
+    ob, cb = b.read_observables()
+    assert np.array_equal(ca, cb) and ca.min() == 1
+    assert np.allclose(oa, ob, rtol=1e-9, atol=1e-12)
+    for lat in lats:
+        lat.destroy()
