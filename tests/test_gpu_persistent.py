@@ -86,19 +86,22 @@ def test_persistent_step_matches_oracle_step_from_equilibrium():
         assert abs(E[j] - ref) <= 2e-6 * abs(ref)
 
 
-def test_bench_small_lattice_workload_resident_equals_streaming():
-    """The mixed small-lattice workload at the size and launch configuration
-    bench.py times (256 samples of L=8 and 256 of L=12, 4 replicas x 8
-    temperatures, FP16 couplings, two lattices per element, shapes chosen by
-    the autotuner): one bench step of 10 MCS with resident launches equals
-    the streaming kernels on every lattice bit for bit, with the same labels,
-    acceptances and counters, and energies and observables equal up to their
-    summation order."""
+@pytest.mark.parametrize("name", ["L8x256_L12x256_R32_f16", "L16_S512_R32_f16"])
+def test_bench_resident_workloads_equal_streaming(name):
+    """The resident workloads at the size and launch configuration bench.py
+    times, with shapes chosen by the autotuner: the mixed small lattices (256
+    samples of L=8 and 256 of L=12, 4 replicas x 8 temperatures; whole
+    replica sets per CTA, PT in the kernel) and the mid-size lattices (512
+    samples of L=16, 2 replicas x 16 temperatures; parts of replica sets per
+    CTA, PT as its own kernel), FP16 couplings, two lattices per element.
+    One bench step of 10 MCS with resident launches equals the streaming
+    kernels on every lattice bit for bit, with the same labels, acceptances
+    and counters, and energies and observables equal up to their summation
+    order."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    name = "L8x256_L12x256_R32_f16"
     w = bench.WORKLOADS[name]
     samples, J, spins, beta = bench.make_inputs(w, 0)
     lats = [bench.build_lattice(hsg, w, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=p)
