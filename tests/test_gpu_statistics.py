@@ -127,24 +127,40 @@ FULL_SIZE = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(FULL_SIZE))
-def test_full_size_throughput_workload_sampled_parity(name):
+# coupling forms: storage precision, layout
+FORMS = {"f16": (hsg.F16, hsg.BATCHED), "bimodal_batched": (hsg.BIMODAL, hsg.BATCHED),
+         "bimodal_plain": (hsg.BIMODAL, hsg.PLAIN)}
+BIMODAL_D = 1.0
+
+
+@pytest.mark.parametrize("name,form", [("L64_S8_R64", "f16"), ("L32_S64_R48", "f16"),
+                                       ("L64_S8_R64", "bimodal_batched"), ("L64_S8_R64", "bimodal_plain")])
+def test_full_size_throughput_workload_sampled_parity(name, form):
     """The launch configurations bench.py times (L=64, 8 samples x 64
     lattices, the default, and L=32, 64 samples x 48 lattices; FP16
-    couplings, two lattices per element, fused sweep in bands of 8 rows): one
-    heat-bath and one overrelaxation sweep from the initial state, checked per
-    half-sweep on whole sampled lattices, plus the fused energies and one PT
-    sweep of every replica set against the oracle."""
+    couplings with two lattices per element, and at L=64 the one-byte bimodal
+    couplings with D = 1 in both layouts; fused sweep in bands of 8 rows):
+    one heat-bath and one overrelaxation sweep from the initial state,
+    checked per half-sweep on whole sampled lattices, plus the fused energies
+    and one PT sweep of every replica set against the oracle."""
     L, S, NT, sampled = FULL_SIZE[name]
+    prec, layout = FORMS[form]
     n_rep, seed = 2, 1
     beta = gi.linear_betas(0.15, 0.75, NT)
-    lat = hsg.Lattice([L] * S, beta, n_replicas=n_rep, coupling_prec=hsg.F16, layout=hsg.BATCHED,
-                      n_or=8, measure_every=10, seed=seed)
+    lat = hsg.Lattice([L] * S, beta, n_replicas=n_rep, coupling_prec=prec, layout=layout,
+                      n_or=8, measure_every=10, seed=seed, bimodal_D=BIMODAL_D)
     plan = lat.get_sweep_plan(0)
     assert plan["fused"] and plan["band_rows"] == 8
-    J = [gi.couplings(L, seed, s, precision="f16") for s in range(S)]
+    J9s = []
     for s in range(S):
-        lat.set_couplings(s, J[s])
+        if prec == hsg.BIMODAL:
+            bits = gi.bimodal_bits(L, seed, s)
+            lat.set_couplings_bimodal(s, bits)
+            J9s.append(oracle.bimodal_j9(bits, BIMODAL_D))
+        else:
+            J6 = gi.couplings(L, seed, s, precision="f16")
+            lat.set_couplings(s, J6)
+            J9s.append(oracle.j9_from_j6(J6))
         lat.set_spins_sample(s, np.stack([gi.random_spins(L, seed, s, j) for j in range(lat.R)]))
 
     for kind in (oracle.HB, oracle.OR):
@@ -154,7 +170,7 @@ def test_full_size_throughput_workload_sampled_parity(name):
         for (s, slot) in sampled:
             after = lat.get_spins(s, slot).astype(np.float64)
             col = _colours(L)
-            J9 = oracle.j9_from_j6(J[s])
+            J9 = J9s[s]
             t = _temp_of(lat)[s, slot]
             ref = before[(s, slot)].copy()
             oracle.half_sweep(L, J9, ref, 0, kind, float(beta[t]), seed, s * lat.R + slot, hb_t)
@@ -175,7 +191,7 @@ def test_full_size_throughput_workload_sampled_parity(name):
     # energies fused into that overrelaxation sweep, and one PT sweep
     E = lat.get_energies()
     for (s, slot) in sampled:
-        ref = oracle.energy(L, oracle.j9_from_j6(J[s]), lat.get_spins(s, slot).astype(np.float64))
+        ref = oracle.energy(L, J9s[s], lat.get_spins(s, slot).astype(np.float64))
         assert abs(E[s, slot] - ref) <= 2e-6 * abs(ref)
     perm = lat.get_perm().copy()
     pt_t = int(lat.get_counters()[1])
