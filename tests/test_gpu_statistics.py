@@ -128,18 +128,20 @@ FULL_SIZE = {
 
 
 # coupling forms: storage precision, layout
-FORMS = {"f16": (hsg.F16, hsg.BATCHED), "bimodal_batched": (hsg.BIMODAL, hsg.BATCHED),
-         "bimodal_plain": (hsg.BIMODAL, hsg.PLAIN)}
+FORMS = {"f16": (hsg.F16, hsg.BATCHED), "f32_plain": (hsg.F32, hsg.PLAIN),
+         "bimodal_batched": (hsg.BIMODAL, hsg.BATCHED), "bimodal_plain": (hsg.BIMODAL, hsg.PLAIN)}
 BIMODAL_D = 1.0
 
 
-@pytest.mark.parametrize("name,form", [("L64_S8_R64", "f16"), ("L32_S64_R48", "f16"),
+@pytest.mark.parametrize("name,form", [("L64_S8_R64", "f16"), ("L32_S64_R48", "f16"), ("L64_S8_R64", "f32_plain"),
                                        ("L64_S8_R64", "bimodal_batched"), ("L64_S8_R64", "bimodal_plain")])
 def test_full_size_throughput_workload_sampled_parity(name, form):
     """The launch configurations bench.py times (L=64, 8 samples x 64
     lattices, the default, and L=32, 64 samples x 48 lattices; FP16
-    couplings with two lattices per element, and at L=64 the one-byte bimodal
-    couplings with D = 1 in both layouts; fused sweep in bands of 8 rows):
+    couplings with two lattices per element, and at L=64 the same
+    FP16-quantised values stored as FP32 with one lattice per element, and
+    the one-byte bimodal couplings with D = 1 in both layouts; fused sweep in
+    bands of 8 rows):
     one heat-bath and one overrelaxation sweep from the initial state,
     checked per half-sweep on whole sampled lattices, plus the fused energies
     and one PT sweep of every replica set against the oracle."""
