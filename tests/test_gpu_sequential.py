@@ -87,3 +87,32 @@ def test_lattices_too_large_for_shared_memory_are_refused():
     with pytest.raises(hsg.HsgError):
         lat.sweep_or_sequential(1)
     assert all(np.array_equal(x, y) for rx, ry in zip(before, state(lat)) for x, y in zip(rx, ry))
+
+
+def test_bench_small_lattice_workload_sampled_site_parity():
+    """The sequential sweep at the size and configuration bench.py times it
+    (the mixed small-lattice workload: 256 samples of L=8 and 256 of L=12, 32
+    lattices each, FP16 couplings, two lattices per element): per-site parity
+    with the oracle on sampled lattices of both sizes, and the whole-sweep
+    drift bound."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    w = bench.WORKLOADS["L8x256_L12x256_R32_f16"]
+    samples, J, spins, beta = bench.make_inputs(w, 0)
+    lat = bench.build_lattice(hsg, w, samples, J, spins, beta, hsg.F16, hsg.BATCHED)
+    del spins
+    sampled = [(0, 0), (0, 1), (255, 31), (256, 0), (300, 17), (511, 31)]
+    before = {sl: lat.get_spins(*sl).astype(np.float64) for sl in sampled}
+    lat.sweep_or_sequential(1)
+    for (s, slot) in sampled:
+        L = lat.Ls[s]
+        J9 = oracle.j9_from_j6(J[s])
+        after = lat.get_spins(s, slot).astype(np.float64)
+        worst = _per_site_parity(L, J9, before[(s, slot)], after)
+        assert 0 < worst <= 2e-5, ((s, slot), worst)
+        ref = before[(s, slot)].copy()
+        oracle.sweep_sequential(L, J9, ref)
+        assert np.abs(after - ref).max() <= 2e-3
+    lat.destroy()
