@@ -216,3 +216,43 @@ def _temp_of(lat):
         for r in range(lat.n_replicas):
             t[s, perm[s, r]] = np.arange(lat.NT)
     return t
+
+
+@pytest.mark.parametrize("name", sorted(FULL_SIZE))
+def test_full_size_measurement_matches_oracle(name):
+    """The measurement (Sec. II.B overlaps and chiral overlaps, App. A.4.3
+    Schwinger-Dyson residual, energies) at the full size of the streaming
+    bench workloads, after one Monte Carlo step: every temperature of the
+    first and the last sample against the oracle's measurement of the same
+    spins and labels."""
+    L, S, NT, _ = FULL_SIZE[name]
+    n_rep, seed = 2, 1
+    beta = gi.linear_betas(0.15, 0.75, NT)
+    lat = hsg.Lattice([L] * S, beta, n_replicas=n_rep, coupling_prec=hsg.F16, layout=hsg.BATCHED,
+                      n_or=8, measure_every=0, seed=seed)
+    J9 = {}
+    for s in range(S):
+        J6 = gi.couplings(L, seed, s, precision="f16")
+        lat.set_couplings(s, J6)
+        if s in (0, S - 1):
+            J9[s] = oracle.j9_from_j6(J6)
+        lat.set_spins_sample(s, np.stack([gi.random_spins(L, seed, s, j) for j in range(lat.R)]))
+    lat.run_steps(1)
+    lat.reset_observables()
+    lat.measure()
+    obs, counts = lat.read_observables()
+    assert np.all(counts == 1)
+    E, perm, N = lat.get_energies(), lat.get_perm(), L ** 3
+    for s in J9:
+        st = lat.get_spins_sample(s).astype(np.float64)
+        ref = np.zeros((NT, hsg.NOBS))
+        for k in range(NT):
+            for r in range(n_rep):
+                e = E[s, perm[s, r, k]] / N
+                ref[k, 0] += e
+                ref[k, 1] += e * e
+                ref[k, 8] += oracle.sd_residual(L, J9[s], st[perm[s, r, k]], 1 / beta[k])
+            ref[k, 2:8] = oracle.measure_pair(L, st[perm[s, 0, k]], st[perm[s, 1, k]])
+        assert np.allclose(obs[s, :, :2], ref[:, :2], rtol=1e-12, atol=0)   # from the same E
+        scale = np.abs(ref).max(axis=0) + 1e-30
+        assert np.all(np.abs(obs[s] - ref) <= 2e-5 * scale + 1e-9), np.abs(obs[s] - ref).max(axis=0)
