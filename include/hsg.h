@@ -309,7 +309,7 @@ hsg_status hsg_philox4x32_10(const uint32_t *in, long n, uint32_t *out);
  * counterpart to this call; it exists for callers that cannot let a library
  * call cudaMalloc or cudaFree -- hosts that give out device memory only from
  * an arena they plan themselves, or latency-critical loops that must never
- * wait in the driver's allocator.
+ * wait in the CUDA driver's allocator.
  *   spins  device float [n_samples*lattices_per_sample][3][N]: component
  *          planes of each lattice, site i = x + L*(y + L*z), lattices of a
  *          sample consecutive;

@@ -298,7 +298,7 @@ hsg_status allow_fused_smem(size_t bytes) {
   return HSG_OK;
 }
 
-// Smallest block limit over a kind's fused kernels, as the driver reports it
+// Smallest block limit over a kind's fused kernels, as the CUDA driver reports it
 // for their register use; 0 if unknown.
 template <int KIND, int V, int PREC>
 int fused_max_threads_one() {
@@ -316,7 +316,7 @@ int fused_max_threads_one() {
 }
 
 // Largest block the fused kernels (heat-bath and overrelaxation) can launch
-// with, as the driver reports it for their register use; 0 if unknown.
+// with, as the CUDA driver reports it for their register use; 0 if unknown.
 int fused_max_threads(int V, int prec) {
   return dispatch(V, prec, [](auto v, auto pr) {
     constexpr int VV = decltype(v)::value, P = decltype(pr)::value;

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Monte Carlo step (Sec. III, App. A.1): the driver is
+"""Pins of the oracle's Monte Carlo step (Sec. III, App. A.1): the step driver is
 exactly the documented composition of sweeps, energies, parallel tempering and
 measurements, and the equilibrium Schwinger-Dyson identity (App. A.4.3) holds
 within errors."""
