@@ -68,12 +68,12 @@ FUSED_SOURCES = ("kernels.cuh", "fused.cuh", "philox.cuh")
 RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
     # profiles/k_sweep_fused_or_L64_S1_R64_f16.md: 387.3 MB for one sample, x8 samples
-    ("69c3411320c0911f", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3098695680,
+    ("7ae4e3bdae527860", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3098738688,
     # profiles/k_sweep_fused_or_L32_S64_R48_f16.md: one launch of the bench's workload
-    ("69c3411320c0911f", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645407744,
+    ("7ae4e3bdae527860", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645332736,
     # profiles/k_persistent_L8x256_L12x256_R32_f16.md: both launches of 10 MCS
-    ("208dcb75e54b7286", "L8x256_L12x256_R32_f16",
-     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 356347136,
+    ("a08c3f36068e5e63", "L8x256_L12x256_R32_f16",
+     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361512192,
 }
 
 

@@ -190,13 +190,7 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
                                             uint32_t i_nat, uint32_t lat0, uint32_t t, uint2 key) {
   if constexpr (KIND == kHB) {
     const uint4 w = philox4x32_10(make_uint4(i_nat, lat0 >> 1, t, kTagHeatBath), key);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const uint32_t lat = lat0 + v;
-      const uint32_t w0 = (lat & 1u) ? w.z : w.x;
-      const uint32_t w1 = (lat & 1u) ? w.w : w.y;
-      heat_bath_draw(h[0][v], h[1][v], h[2][v], beta[v], w0, w1, s[0][v], s[1][v], s[2][v]);
-    }
+    heat_bath_site<V>(h, beta, w, lat0, s);
   } else {
     overrelax_v<V>(h, s);
   }

@@ -248,6 +248,100 @@ __device__ __forceinline__ void heat_bath_draw(float hx, float hy, float hz, flo
   sz = fmaf(u, nz, st * az);
 }
 
+// Heat-bath draws of the two lattices of one site: the operations of
+// heat_bath_draw lane for lane, with the multiply-add arithmetic of the common
+// case (kappa > 1/2 in both lanes, no antipole correction) as FP32x2
+// instructions, which round each lane as the scalar ones do.  Any other case
+// is drawn by heat_bath_draw itself, so the draws equal it bit for bit.
+__device__ __forceinline__ void heat_bath_draw2(const float (&h)[3][2], const float (&beta)[2], uint32_t w0a,
+                                                uint32_t w1a, uint32_t w0b, uint32_t w1b, float (&s)[3][2]) {
+  const float2 hx = make_float2(h[0][0], h[0][1]), hy = make_float2(h[1][0], h[1][1]),
+               hz = make_float2(h[2][0], h[2][1]);
+  const float2 hh = __ffma2_rn(hx, hx, __ffma2_rn(hy, hy, __fmul2_rn(hz, hz)));
+  const float2 inv = make_float2((hh.x > 0.0f) ? rsqrtf(hh.x) : 0.0f, (hh.y > 0.0f) ? rsqrtf(hh.y) : 0.0f);
+  const float2 kappa = __fmul2_rn(make_float2(beta[0], beta[1]), __fmul2_rn(hh, inv));
+  const float2 r0 = make_float2(uniform23(w0a), uniform23(w0b));
+  const float2 e2k = make_float2(__expf(-2.0f * kappa.x), __expf(-2.0f * kappa.y));
+  const float2 nr0 = make_float2(-r0.x, -r0.y);
+  const float2 one = make_float2(1.0f, 1.0f);
+  const float2 y = __ffma2_rn(nr0, e2k, r0);
+  const float2 a_lo = __fadd2_rn(one, make_float2(-y.x, -y.y));
+  const float2 a_hi = __ffma2_rn(r0, e2k, __fadd2_rn(one, nr0));
+  const float lfx = __logf((y.x < 0.5f) ? a_lo.x : a_hi.x), lfy = __logf((y.y < 0.5f) ? a_lo.y : a_hi.y);
+  const float2 c7 = make_float2(1.0f / 7.0f, 1.0f / 7.0f), c6 = make_float2(1.0f / 6.0f, 1.0f / 6.0f),
+               c5 = make_float2(0.2f, 0.2f), c4 = make_float2(0.25f, 0.25f),
+               c3 = make_float2(1.0f / 3.0f, 1.0f / 3.0f), c2 = make_float2(0.5f, 0.5f);
+  const float2 ps = __fmul2_rn(
+      y, __ffma2_rn(y, __ffma2_rn(y, __ffma2_rn(y, __ffma2_rn(y, __ffma2_rn(y, __ffma2_rn(y, c7, c6), c5), c4), c3),
+                                  c2), one));
+  const float lgx = (y.x < 0.0625f) ? -ps.x : lfx, lgy = (y.y < 0.0625f) ? -ps.y : lfy;
+  float2 w = make_float2(__fdividef(-lgx, kappa.x), __fdividef(-lgy, kappa.y));
+  w.x = fminf(fmaxf(w.x, 0.0f), 2.0f);
+  w.y = fminf(fmaxf(w.y, 0.0f), 2.0f);
+  if (!(kappa.x > 0.5f && kappa.y > 0.5f) || w.x > 1.99f || w.y > 1.99f) {
+    heat_bath_draw(h[0][0], h[1][0], h[2][0], beta[0], w0a, w1a, s[0][0], s[1][0], s[2][0]);
+    heat_bath_draw(h[0][1], h[1][1], h[2][1], beta[1], w0b, w1b, s[0][1], s[1][1], s[2][1]);
+    return;
+  }
+  const float2 nw = make_float2(-w.x, -w.y);
+  const float2 wc = __fadd2_rn(make_float2(2.0f, 2.0f), nw);
+  const float2 u = __fadd2_rn(one, nw);
+  const float2 ww = __fmul2_rn(w, wc);
+  const float2 w2 = make_float2(fmaxf(ww.x, 0.0f), fmaxf(ww.y, 0.0f));
+  const float2 sq = __fmul2_rn(w2, make_float2(rsqrtf(w2.x), rsqrtf(w2.y)));
+  const float2 st = make_float2((w2.x > 0.0f) ? sq.x : 0.0f, (w2.y > 0.0f) ? sq.y : 0.0f);
+  const float2 r1 = make_float2(uniform23(w1a), uniform23(w1b));
+  const float2 phi = __fmul2_rn(make_float2(6.283185307179586f, 6.283185307179586f),
+                                __fadd2_rn(r1, make_float2(-0.5f, -0.5f)));
+  float2 sp, cp;
+  __sincosf(phi.x, &sp.x, &cp.x);
+  __sincosf(phi.y, &sp.y, &cp.y);
+  sp = make_float2(-sp.x, -sp.y);
+  cp = make_float2(-cp.x, -cp.y);
+  const float2 px = __fmul2_rn(hx, inv), py = __fmul2_rn(hy, inv), pz = __fmul2_rn(hz, inv);
+  const float2 nx = make_float2((hh.x > 0.0f) ? px.x : 0.0f, (hh.y > 0.0f) ? px.y : 0.0f);
+  const float2 ny = make_float2((hh.x > 0.0f) ? py.x : 0.0f, (hh.y > 0.0f) ? py.y : 0.0f);
+  const float2 nz = make_float2((hh.x > 0.0f) ? pz.x : 1.0f, (hh.y > 0.0f) ? pz.y : 1.0f);
+  const float2 sgn = make_float2(copysignf(1.0f, nz.x), copysignf(1.0f, nz.y));
+  const float2 sn = __fadd2_rn(sgn, nz);
+  const float2 p = make_float2(__fdividef(-1.0f, sn.x), __fdividef(-1.0f, sn.y));
+  const float2 q = __fmul2_rn(__fmul2_rn(nx, ny), p);
+  const float2 e1x = __ffma2_rn(__fmul2_rn(__fmul2_rn(sgn, nx), nx), p, one);
+  const float2 e1y = __fmul2_rn(sgn, q);
+  const float2 e1z = __fmul2_rn(make_float2(-sgn.x, -sgn.y), nx);
+  const float2 e2x = q;
+  const float2 e2y = __ffma2_rn(__fmul2_rn(ny, ny), p, sgn);
+  const float2 e2z = make_float2(-ny.x, -ny.y);
+  const float2 ax = __ffma2_rn(cp, e1x, __fmul2_rn(sp, e2x));
+  const float2 ay = __ffma2_rn(cp, e1y, __fmul2_rn(sp, e2y));
+  const float2 az = __ffma2_rn(cp, e1z, __fmul2_rn(sp, e2z));
+  const float2 sx = __ffma2_rn(u, nx, __fmul2_rn(st, ax));
+  const float2 sy = __ffma2_rn(u, ny, __fmul2_rn(st, ay));
+  const float2 sz = __ffma2_rn(u, nz, __fmul2_rn(st, az));
+  s[0][0] = sx.x; s[0][1] = sx.y;
+  s[1][0] = sy.x; s[1][1] = sy.y;
+  s[2][0] = sz.x; s[2][1] = sz.y;
+}
+
+// The heat-bath draws of the V lattices lat0 .. lat0+V-1 of one site from one
+// Philox block w: a lattice takes the words (x, y) if its index is even and
+// (z, w) if it is odd.
+template <int V>
+__device__ __forceinline__ void heat_bath_site(const float (&h)[3][V], const float (&beta)[V], uint4 w,
+                                               uint32_t lat0, float (&s)[3][V]) {
+  if constexpr (V == 2) {
+    const bool odd = (lat0 & 1u) != 0;
+    heat_bath_draw2(h, beta, odd ? w.z : w.x, odd ? w.w : w.y, odd ? w.x : w.z, odd ? w.y : w.w, s);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const uint32_t lat = lat0 + v;
+      heat_bath_draw(h[0][v], h[1][v], h[2][v], beta[v], (lat & 1u) ? w.z : w.x, (lat & 1u) ? w.w : w.y,
+                     s[0][v], s[1][v], s[2][v]);
+    }
+  }
+}
+
 // Overrelaxation: reflection of s about h, s' = 2h(h.s)/h^2 - s.
 __device__ __forceinline__ void overrelax(float hx, float hy, float hz, float& sx, float& sy, float& sz) {
   const float hh = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
@@ -380,15 +474,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_half(SweepParams p) {
       const int sg = b.sample_ids[sb];
       const uint32_t lat0 = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(g * V);
       const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i_nat), lat0 >> 1, t, kTagHeatBath), p.key);
-      float out[3][V];
+      float out[3][V], beta[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const uint32_t lat = lat0 + v;
-        const float beta = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + g * V + v]];
-        const uint32_t w0 = (lat & 1u) ? w.z : w.x;
-        const uint32_t w1 = (lat & 1u) ? w.w : w.y;
-        heat_bath_draw(h[0][v], h[1][v], h[2][v], beta, w0, w1, out[0][v], out[1][v], out[2][v]);
-      }
+      for (int v = 0; v < V; ++v) beta[v] = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + g * V + v]];
+      heat_bath_site<V>(h, beta, w, lat0, out);
       store_spin<V>(base, plane, i, out);
     } else {
       float o[3][V];

@@ -316,12 +316,10 @@ __device__ __forceinline__ void resident_half_sweep(float* sp, const void* Js, c
           const uint32_t lat0 = lat_base + static_cast<uint32_t>(g * V);
           const uint4 u =
               philox4x32_10(make_uint4(static_cast<uint32_t>(r.i_nat), lat0 >> 1, t, kTagHeatBath), key);
+          float bq[V];
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const uint32_t lat = lat0 + v;
-            heat_bath_draw(h[q][0][v], h[q][1][v], h[q][2][v], beta_lat[g * V + v], (lat & 1u) ? u.z : u.x,
-                           (lat & 1u) ? u.w : u.y, o[0][v], o[1][v], o[2][v]);
-          }
+          for (int v = 0; v < V; ++v) bq[v] = beta_lat[g * V + v];
+          heat_bath_site<V>(h[q], bq, u, lat0, o);
         } else {
           lds_plane<V>(own, plane, ic, o);
           overrelax_v<V>(h[q], o);
