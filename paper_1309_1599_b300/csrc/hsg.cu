@@ -145,8 +145,7 @@ void free_ctx(hsg_ctx* h) {
   cudaFree(h->d_status);
   for (Bucket& b : h->buckets) {
     cudaFree(b.d_samples);
-    cudaFree(b.d_spins[0]);
-    cudaFree(b.d_spins[1]);
+    cudaFree(b.d_spins[0]);  // d_spins[1] lies in the same allocation
     cudaFree(b.d_J);
     cudaFree(b.d_epart);
     cudaFree(b.d_mpart);
@@ -856,8 +855,18 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     const size_t n_spin = static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
     hsg_status st;
     if ((st = dalloc(&b.d_samples, b.S_b)) != HSG_OK) return bail(st);
-    if ((st = dalloc(&b.d_spins[0], n_spin)) != HSG_OK) return bail(st);
-    if (b.fused && (st = dalloc(&b.d_spins[1], n_spin)) != HSG_OK) return bail(st);
+    // The fused sweep reads one spin buffer and writes the other at nearly
+    // the same offsets.  Both share one allocation, the second starting half
+    // a 2 MiB page (mod 2 MiB) after the first: with the two at equal offsets
+    // modulo 2 MiB (separate allocations) the L = 64 overrelaxation sweep
+    // ran 2.8% slower on some boxes and builds.
+    size_t pad = 0;
+    if (b.fused) {
+      const size_t page = size_t(2) << 20, rem = (n_spin * sizeof(float)) % page;
+      pad = ((page / 2 + page - rem) % page) / sizeof(float);
+    }
+    if ((st = dalloc(&b.d_spins[0], b.fused ? 2 * n_spin + pad : n_spin)) != HSG_OK) return bail(st);
+    if (b.fused) b.d_spins[1] = b.d_spins[0] + n_spin + pad;
     const size_t jbytes = static_cast<size_t>(b.S_b) * 3 * b.N * bond_bytes(h->prec);
     if ((st = dalloc(reinterpret_cast<char**>(&b.d_J), jbytes)) != HSG_OK) return bail(st);
     if ((st = dalloc(&b.d_epart, static_cast<size_t>(b.S_b) * h->R * std::max(b.sweep_chunks, b.n_bands))) != HSG_OK)
