@@ -128,6 +128,15 @@ typedef struct {
   double bimodal_D;       /* HSG_BIMODAL: the magnitude D >= 0 of the
                              anisotropic couplings (the paper uses 0.5 and 1);
                              ignored by the other formats */
+  int fused_groups;       /* fused sweep: lattice groups (of the layout's
+                             lattices per element) that each thread updates
+                             against one read of each coupling, for both the
+                             heat-bath and the overrelaxation kernel; 0 =
+                             library choice (1 until hsg_autotune picks per
+                             kernel), 1, or 2 (batched layout with a multiple
+                             of 4 lattices per sample; HSG_EINVAL otherwise,
+                             or if L cannot be tiled with it).  The spins do
+                             not depend on it. */
 } hsg_config;
 
 /* Create a context: validates cfg (copied; the caller's arrays may be freed
@@ -249,8 +258,10 @@ hsg_status hsg_set_counters(hsg_t h, const uint64_t in[3]);
 
 /* How the sweeps of `sample` run: out[0] = 1 for the fused one-pass kernel,
  * 0 for two half-sweep kernels; out[1] = rows per band of the fused kernel
- * (L for whole planes); out[2] = kernel launches per sweep. */
-hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]);
+ * (L for whole planes); out[2] = kernel launches per sweep; out[3], out[4] =
+ * lattice groups per thread of the fused overrelaxation and heat-bath
+ * kernels (0 for the half-sweeps). */
+hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[5]);
 
 /* Resident steps (persistent contexts) of `sample`'s lattice size: out[0] =
  * bond residency (0 global, 1 shared as stored, 2 shared as FP32), out[1] =
@@ -261,13 +272,13 @@ hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]);
 /* Autotuner (Sec. III's sweeps; the tiling is free, the results do not
  * depend on it).  For each lattice size of the context it times the
  * candidate launch shapes on the context's own couplings and spins and keeps
- * the fastest: the band height of the fused sweep, or the two-pass
- * half-sweeps instead (timed as overrelaxation sweeps whose output is
- * discarded, or that run on a copy of the state) and, for persistent
- * contexts, the groups
- * per work item and threads per CTA of the resident steps (timed on scratch
- * copies of the spins, labels, energies and acceptances).  The state is not
- * changed.  A choice is remembered for the process per (L, lattices per
+ * the fastest: the band height and lattice groups per thread of the fused
+ * overrelaxation sweep, or the two-pass half-sweeps instead (timed as
+ * overrelaxation sweeps whose output is discarded, or that run on a copy of
+ * the state), then the groups per thread of the fused heat-bath sweep at
+ * that band height, and, for persistent contexts, the groups per work item
+ * and threads per CTA of the resident steps (timed on scratch copies of the
+ * spins, labels, energies and acceptances).  The state is not changed.  A choice is remembered for the process per (L, lattices per
  * element, precision, lattices of that L, N_T, bond residency), so later
  * contexts of the same
  * shape take it without timing.  Synchronous; a new shape must beat the
@@ -338,7 +349,7 @@ const char *hsg_last_error(void);
 
 /* ABI version of this header. */
 int hsg_version(void);
-#define HSG_VERSION 2  /* bumped with every change of hsg_config or of a signature */
+#define HSG_VERSION 3  /* bumped with every change of hsg_config or of a signature */
 
 #ifdef __cplusplus
 }

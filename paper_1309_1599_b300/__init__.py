@@ -20,7 +20,7 @@ __all__ = ["Lattice", "HsgError", "load_library", "philox4x32_10", "library_path
            "F32", "F16", "PLAIN", "BATCHED", "SWEEP_AUTO", "SWEEP_TWO_PASS", "NOBS",
            "OBS_NAMES"]
 
-ABI_VERSION = 2            # HSG_VERSION of include/hsg.h
+ABI_VERSION = 3            # HSG_VERSION of include/hsg.h
 F32, F16, BIMODAL = 0, 1, 2
 PLAIN, BATCHED = 0, 1
 SWEEP_AUTO, SWEEP_TWO_PASS = 0, 1
@@ -52,7 +52,7 @@ class _Config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
                 ("timeout_cycles", ctypes.c_longlong), ("sweep_kernel", ctypes.c_int),
                 ("band_rows", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("bimodal_D", ctypes.c_double)]
+                ("bimodal_D", ctypes.c_double), ("fused_groups", ctypes.c_int)]
 
 
 _SIGNATURES = {
@@ -188,7 +188,7 @@ class Lattice:
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
                  timeout_cycles=0, sweep_kernel=SWEEP_AUTO, band_rows=0, persistent=False,
-                 bimodal_D=1.0):
+                 bimodal_D=1.0, fused_groups=0):
         lib = load_library()
         _require_gpu()
         if np.isscalar(L):
@@ -219,6 +219,7 @@ class Lattice:
         cfg.band_rows = int(band_rows)
         cfg.persistent = 1 if persistent else 0
         cfg.bimodal_D = float(bimodal_D)
+        cfg.fused_groups = int(fused_groups)
         self.coupling_prec = int(coupling_prec)
         self.bimodal_D = float(bimodal_D)
         h = ctypes.c_void_p()
@@ -374,9 +375,10 @@ class Lattice:
         _check(self._lib.hsg_set_counters(self._h, _ptr(a)))
 
     def get_sweep_plan(self, sample: int = 0) -> dict:
-        out = np.zeros(3, dtype=np.int32)
+        out = np.zeros(5, dtype=np.int32)
         _check(self._lib.hsg_get_sweep_plan(self._h, sample, _ptr(out)))
-        return {"fused": bool(out[0]), "band_rows": int(out[1]), "launches_per_sweep": int(out[2])}
+        return {"fused": bool(out[0]), "band_rows": int(out[1]), "launches_per_sweep": int(out[2]),
+                "groups_per_thread_or": int(out[3]), "groups_per_thread_hb": int(out[4])}
 
     def get_resident_plan(self, sample: int = 0) -> dict:
         out = np.zeros(4, dtype=np.int32)

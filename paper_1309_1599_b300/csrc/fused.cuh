@@ -145,44 +145,65 @@ __device__ __forceinline__ void copy3(float (&d)[3][V], const float (&s)[3][V]) 
 }
 
 // Local field h = sum over the six bonds of J s_neighbour (J symmetric) of
-// one site, accumulated as in k_sweep_half (forward bonds x+1, y+1, z+1 and
-// backward bonds x-1, y-1, z-1 in two partial sums).  Jb points at the
-// sample's couplings; pos, pos_xm, pos_ym, pos_zm are the storage positions
-// of the site and of its neighbours at x-1, y-1, z-1 (whose +x, +y, +z bonds
-// are this site's -x, -y, -z bonds).  jz_up / jz_dn: the +z / -z bond,
-// already loaded by the caller (or null: load it here).
-template <int V, int PREC>
-__device__ __forceinline__ void site_field(const void* Jb, float D, int N, int pos, int pos_xm, int pos_ym, int pos_zm,
-                                           const float (&xp)[3][V], const float (&xm)[3][V],
-                                           const float (&yu)[3][V], const float (&yd)[3][V],
-                                           const float (&zu)[3][V], const float (&zd)[3][V], float (&h)[3][V],
-                                           const float* jz_up = nullptr, const float* jz_dn = nullptr) {
-  float hf[3][V], hb[3][V], j[6];
-  zero3<V>(hf);
-  zero3<V>(hb);
+// one site in each of GP lattice groups, accumulated as in k_sweep_half
+// (forward bonds x+1, y+1, z+1 and backward bonds x-1, y-1, z-1 in two
+// partial sums).  Each bond is loaded and converted once and serves all GP
+// groups; every lattice's sums are those of a single group, so the result
+// does not depend on GP.  Jb points at the sample's couplings; pos, pos_xm,
+// pos_ym, pos_zm are the storage positions of the site and of its neighbours
+// at x-1, y-1, z-1 (whose +x, +y, +z bonds are this site's -x, -y, -z
+// bonds).  jz_up / jz_dn: the +z / -z bond, already loaded by the caller (or
+// null: load it here).
+template <int GP, int V, int PREC>
+__device__ __forceinline__ void site_field(const void* Jb, float D, int N, int pos, int pos_xm, int pos_ym,
+                                           int pos_zm, const float (&xp)[GP][3][V], const float (&xm)[GP][3][V],
+                                           const float (&yu)[GP][3][V], const float (&yd)[GP][3][V],
+                                           const float (&zu)[GP][3][V], const float (&zd)[GP][3][V],
+                                           float (&h)[GP][3][V], const float* jz_up = nullptr,
+                                           const float* jz_dn = nullptr) {
+  float hf[GP][3][V], hb[GP][3][V], j[6];
+#pragma unroll
+  for (int g = 0; g < GP; ++g) {
+    zero3<V>(hf[g]);
+    zero3<V>(hb[g]);
+  }
   load_bond<PREC>(Jb, pos, j, D);
-  add_bond<V>(j, xp, hf);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) add_bond<V>(j, xp[g], hf[g]);
   load_bond<PREC>(Jb, N + pos, j, D);
-  add_bond<V>(j, yu, hf);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) add_bond<V>(j, yu[g], hf[g]);
   if (jz_up) {
 #pragma unroll
     for (int e = 0; e < 6; ++e) j[e] = jz_up[e];
   } else {
     load_bond<PREC>(Jb, 2 * N + pos, j, D);
   }
-  add_bond<V>(j, zu, hf);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) add_bond<V>(j, zu[g], hf[g]);
   load_bond<PREC>(Jb, pos_xm, j, D);
-  add_bond<V>(j, xm, hb);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) add_bond<V>(j, xm[g], hb[g]);
   load_bond<PREC>(Jb, N + pos_ym, j, D);
-  add_bond<V>(j, yd, hb);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) add_bond<V>(j, yd[g], hb[g]);
   if (jz_dn) {
 #pragma unroll
     for (int e = 0; e < 6; ++e) j[e] = jz_dn[e];
   } else {
     load_bond<PREC>(Jb, 2 * N + pos_zm, j, D);
   }
-  add_bond<V>(j, zd, hb);
-  combine_field<V>(hf, hb, h);
+#pragma unroll
+  for (int g = 0; g < GP; ++g) {
+    add_bond<V>(j, zd[g], hb[g]);
+    combine_field<V>(hf[g], hb[g], h[g]);
+  }
+}
+
+// A site's V lattices as a set of one group (same storage), for site_field.
+template <int V>
+__device__ __forceinline__ float (&one_group(float (&s)[3][V]))[1][3][V] {
+  return *reinterpret_cast<float(*)[1][3][V]>(&s);
 }
 
 template <int KIND, int V>
@@ -196,15 +217,33 @@ __device__ __forceinline__ void update_site(const float (&h)[3][V], float (&s)[3
   }
 }
 
+// The site of every one of the GP groups: group g's planes follow group
+// g-1's in a slot (gstride floats apart) and in global memory.
+template <int GP, int V>
+__device__ __forceinline__ void lds_sites(const float* p, float (&s)[GP][3][V], int comp_stride, int gstride) {
+#pragma unroll
+  for (int g = 0; g < GP; ++g) lds_site<V>(p + g * gstride, s[g], comp_stride);
+}
+
+// Registers per thread of the fused sweep: 96 holds one group's working set
+// with two CTAs per SM; two groups per thread run one CTA per SM (their ring
+// takes twice the shared memory) and get the registers that frees.
+template <int GP>
+constexpr int fused_max_regs() {
+  return GP == 1 ? 96 : 168;
+}
+
 // LT, BT: the lattice size and band height as compile-time constants (the
 // common tilings), or 0 to take them from p at run time.  With constants the
 // ring-slot strides and plane parities fold into immediate offsets once the
-// march over z is unrolled by the ring period.
-template <int KIND, int V, int PREC, int LT = 0, int BT = 0>
-__global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
+// march over z is unrolled by the ring period.  GP: lattice groups (of V
+// lattices of one sample) per CTA; a thread updates its sites in all GP
+// groups, so each bond load and conversion serves GP * V lattices.
+template <int KIND, int V, int PREC, int LT = 0, int BT = 0, int GP = 1>
+__global__ void __maxnreg__(fused_max_regs<GP>()) k_sweep_fused(FusedParams p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t bars[kFusedSlots + 1];  // [kFusedSlots]: never completed
-  __shared__ double s_red[V][kFusedMaxThreads / 32];
+  __shared__ double s_red[GP * V][kFusedMaxThreads / 32];
   __shared__ int s_failed;
 
   const int L = LT > 0 ? LT : p.L, half = L >> 1, N = L * L * L;
@@ -214,10 +253,12 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   const int slot_rows = full ? L : band_rows + 4;
   const int row_f = L * V;                        // floats per staged row
   const int comp_f = slot_rows * row_f;           // floats per component in a slot
-  const int slot_f = 3 * comp_f;
-  const int gi = blockIdx.x / n_bands;
-  const int band = blockIdx.x - gi * n_bands;
-  const int sb = gi / p.G, g = gi - sb * p.G;
+  const int grp_f = 3 * comp_f;                   // floats per group in a slot
+  const int slot_f = GP * grp_f;
+  const int gs = blockIdx.x / n_bands;            // set of GP groups
+  const int band = blockIdx.x - gs * n_bands;
+  const int GS = p.G / GP;                        // sets per sample
+  const int sb = gs / GS, g0 = (gs - sb * GS) * GP;
   const int y0 = band * band_rows;
   const int tid = threadIdx.x;
   const int rows_t = full ? L : band_rows + 2;
@@ -232,27 +273,35 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   const int k_up = (k + 1 == half) ? 0 : k + 1;
   const int k_dn = (k == 0) ? half - 1 : k - 1;
   const int y_dn = (y == 0) ? L - 1 : y - 1;
-  const size_t gbase = static_cast<size_t>(gi) * 3 * N * V;
+  const size_t plane_g = static_cast<size_t>(N) * V;   // component stride in global memory
+  const size_t gbase = static_cast<size_t>(gs) * GP * 3 * plane_g;
   const float* in_g = p.in + gbase;
   float* out_g = p.out + gbase;
-  const size_t plane_g = static_cast<size_t>(N) * V;   // component stride in global memory
   // couplings of this sample (element size depends on the storage precision)
   const void* Jb = sample_bonds<PREC>(p.J, sb, N);
   const bool want_energy = (p.e_partial != nullptr);
   const int LL = L * L;
   const int yrow = y * L, ydrow = y_dn * L;
 
-  float beta[V];
-  uint32_t lat0 = 0, t_hb = 0;
+  float beta[GP][V];
+  uint32_t lat0[GP], t_hb = 0;
   if constexpr (KIND == kHB) {
     const int sg = p.sample_ids[sb];
-    lat0 = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(g * V);
     t_hb = p.counters[0];
 #pragma unroll
-    for (int v = 0; v < V; ++v) beta[v] = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + g * V + v]];
+    for (int g = 0; g < GP; ++g) {
+      lat0[g] = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>((g0 + g) * V);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        beta[g][v] = p.beta_f[p.temp_of[static_cast<size_t>(sg) * p.R + (g0 + g) * V + v]];
+    }
   } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) beta[v] = 0.0f;
+    for (int g = 0; g < GP; ++g) {
+      lat0[g] = 0;
+#pragma unroll
+      for (int v = 0; v < V; ++v) beta[g][v] = 0.0f;
+    }
   }
 
   const uint32_t slot_bytes = static_cast<uint32_t>(slot_f) * 4u;
@@ -263,7 +312,7 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
     const int s = (vp + 1) & 3;
     float* dst = smem + s * slot_f;
     mbar_expect_tx(&bars[s], slot_bytes);
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 3 * GP; ++c) {  // component c % 3 of group c / 3
       int done = 0;
       while (done < slot_rows) {
         const int yy = (ystart + done) % L;
@@ -275,7 +324,8 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
     }
   };
   auto parity_of = [](int vp) -> uint32_t { return static_cast<uint32_t>(((vp + 1) >> 2) & 1); };
-  // Site (row rr, x-parity a, pair kk) of the slot holding virtual plane vp.
+  // Site (row rr, x-parity a, pair kk) of group 0 in the slot holding virtual
+  // plane vp.
   auto at = [&](int vp, int rr, int a, int kk) -> float* {
     return smem + ((vp + 1) & 3) * slot_f + rr * row_f + (a * half + kk) * V;
   };
@@ -297,12 +347,17 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   // again) and of the current plane; everything else is read from the
   // resident slots: planes z-1, z (in-plane neighbours, old white spins,
   // new black spins) and z+1.
-  float Bm2[3][V], Bm1[3][V], B0[3][V];
-  zero3<V>(Bm2);
-  zero3<V>(Bm1);
-  double e_acc[V];
+  float Bm2[GP][3][V], Bm1[GP][3][V], B0[GP][3][V];
 #pragma unroll
-  for (int v = 0; v < V; ++v) e_acc[v] = 0.0;
+  for (int g = 0; g < GP; ++g) {
+    zero3<V>(Bm2[g]);
+    zero3<V>(Bm1[g]);
+  }
+  double e_acc[GP][V];
+#pragma unroll
+  for (int g = 0; g < GP; ++g)
+#pragma unroll
+    for (int v = 0; v < V; ++v) e_acc[g][v] = 0.0;
 
   int first_unwaited = -1;  // lowest virtual plane not yet known complete
   bool ok = true;
@@ -328,49 +383,56 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       const int q_dn = (q == 0) ? L - 1 : q - 1;
       const int aw = ab;              // white site of plane z-1 in this column
       const int plq = q * LL;
-      float xp[3][V], xm[3][V], yu[3][V], yd[3][V], zu[3][V], zd[3][V], h[3][V];
-      lds_site<V>(at(z, r, ab, k), B0, comp_f);
-      lds_site<V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f);
-      lds_site<V>(at(z, r, ab ^ 1, ab ? k : k_dn), xm, comp_f);
-      lds_site<V>(at(z, r_up, ab, k), yu, comp_f);
-      lds_site<V>(at(z, r_dn, ab, k), yd, comp_f);
-      lds_site<V>(at(z + 1, r, ab, k), zu, comp_f);
-      lds_site<V>(at(z - 1, r, ab, k), zd, comp_f);
+      float xp[GP][3][V], xm[GP][3][V], yu[GP][3][V], yd[GP][3][V], zu[GP][3][V], zd[GP][3][V], h[GP][3][V];
+      lds_sites<GP, V>(at(z, r, ab, k), B0, comp_f, grp_f);
+      lds_sites<GP, V>(at(z, r, ab ^ 1, ab ? k_up : k), xp, comp_f, grp_f);
+      lds_sites<GP, V>(at(z, r, ab ^ 1, ab ? k : k_dn), xm, comp_f, grp_f);
+      lds_sites<GP, V>(at(z, r_up, ab, k), yu, comp_f, grp_f);
+      lds_sites<GP, V>(at(z, r_dn, ab, k), yd, comp_f, grp_f);
+      lds_sites<GP, V>(at(z + 1, r, ab, k), zu, comp_f, grp_f);
+      lds_sites<GP, V>(at(z - 1, r, ab, k), zd, comp_f, grp_f);
       // the z bond between this column's sites at planes z-1 and z: the
       // black site's -z bond and the +z bond of the white site updated below
       float jz[6];
       load_bond<PREC>(Jb, 2 * static_cast<size_t>(N) + pz_dn * LL + yrow + ab * half + k, jz, p.D);
       {
         const int pl = pz * LL;
-        site_field<V, PREC>(Jb, p.D, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
-                            pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k, xp, xm, yu, yd, zu,
-                            zd, h, nullptr, jz);
+        site_field<GP, V, PREC>(Jb, p.D, N, pl + yrow + ab * half + k, pl + yrow + (ab ? k : half + k_dn),
+                                pl + ydrow + ab * half + k, pz_dn * LL + yrow + ab * half + k, xp, xm, yu, yd,
+                                zu, zd, h, nullptr, jz);
       }
       const uint32_t i_nat = static_cast<uint32_t>(2 * k + ab + L * (y + L * pz));
-      update_site<KIND, V>(h, B0, beta, i_nat, lat0, t_hb, p.key);
-      sts_site<V>(at(z, r, ab, k), B0, comp_f);
+#pragma unroll
+      for (int g = 0; g < GP; ++g) {
+        update_site<KIND, V>(h[g], B0[g], beta[g], i_nat, lat0[g], t_hb, p.key);
+        sts_site<V>(at(z, r, ab, k) + g * grp_f, B0[g], comp_f);
+      }
 
       // white site of plane z-1 from the new black spins
       if (do_white) {
-        float w[3][V];
-        lds_site<V>(at(z - 1, r, aw, k), w, comp_f);
-        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k_up : k), xp, comp_f);
-        lds_site<V>(at(z - 1, r, aw ^ 1, aw ? k : k_dn), xm, comp_f);
-        lds_site<V>(at(z - 1, r_up, aw, k), yu, comp_f);
-        lds_site<V>(at(z - 1, r_dn, aw, k), yd, comp_f);
-        site_field<V, PREC>(Jb, p.D, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
-                            plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k, xp, xm, yu, yd, B0,
-                            Bm2, h, jz, nullptr);
+        float w[GP][3][V];
+        lds_sites<GP, V>(at(z - 1, r, aw, k), w, comp_f, grp_f);
+        lds_sites<GP, V>(at(z - 1, r, aw ^ 1, aw ? k_up : k), xp, comp_f, grp_f);
+        lds_sites<GP, V>(at(z - 1, r, aw ^ 1, aw ? k : k_dn), xm, comp_f, grp_f);
+        lds_sites<GP, V>(at(z - 1, r_up, aw, k), yu, comp_f, grp_f);
+        lds_sites<GP, V>(at(z - 1, r_dn, aw, k), yd, comp_f, grp_f);
+        site_field<GP, V, PREC>(Jb, p.D, N, plq + yrow + aw * half + k, plq + yrow + (aw ? k : half + k_dn),
+                                plq + ydrow + aw * half + k, q_dn * LL + yrow + aw * half + k, xp, xm, yu, yd,
+                                B0, Bm2, h, jz, nullptr);
         const uint32_t iw_nat = static_cast<uint32_t>(2 * k + aw + L * (y + L * q));
-        update_site<KIND, V>(h, w, beta, iw_nat, lat0, t_hb, p.key);
-        if (want_energy) {
-#pragma unroll
-          for (int v = 0; v < V; ++v)
-            e_acc[v] += static_cast<double>(fmaf(w[0][v], h[0][v], fmaf(w[1][v], h[1][v], w[2][v] * h[2][v])));
-        }
         float* dst = out_g + static_cast<size_t>(plq + yrow) * V;
-        stg_site<V>(dst + ((aw ^ 1) * half + k) * V, Bm1, plane_g);
-        stg_site<V>(dst + (aw * half + k) * V, w, plane_g);
+#pragma unroll
+        for (int g = 0; g < GP; ++g) {
+          update_site<KIND, V>(h[g], w[g], beta[g], iw_nat, lat0[g], t_hb, p.key);
+          if (want_energy) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+              e_acc[g][v] += static_cast<double>(
+                  fmaf(w[g][0][v], h[g][0][v], fmaf(w[g][1][v], h[g][1][v], w[g][2][v] * h[g][2][v])));
+          }
+          stg_site<V>(dst + g * 3 * plane_g + ((aw ^ 1) * half + k) * V, Bm1[g], plane_g);
+          stg_site<V>(dst + g * 3 * plane_g + (aw * half + k) * V, w[g], plane_g);
+        }
       }
     }
     // Generic-proxy accesses of the slot being refilled must precede the
@@ -386,8 +448,11 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
       issue(z + 3);
       issued = z + 3;
     }
-    copy3<V>(Bm2, Bm1);
-    copy3<V>(Bm1, B0);
+#pragma unroll
+    for (int g = 0; g < GP; ++g) {
+      copy3<V>(Bm2[g], Bm1[g]);
+      copy3<V>(Bm1[g], B0[g]);
+    }
   }
 
   if (failed) {
@@ -404,16 +469,18 @@ __global__ void __maxnreg__(96) k_sweep_fused(FusedParams p) {
   if (p.e_partial != nullptr) {
     const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const double d = warp_sum(-e_acc[v]);
-      if (lane == 0) s_red[v][warp] = d;
-    }
+    for (int g = 0; g < GP; ++g)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const double d = warp_sum(-e_acc[g][v]);
+        if (lane == 0) s_red[g * V + v][warp] = d;
+      }
     __syncthreads();
-    if (tid < V) {
+    if (tid < GP * V) {
       double acc = 0.0;
       const int nw = (blockDim.x + 31) >> 5;
       for (int w = 0; w < nw; ++w) acc += s_red[tid][w];
-      const size_t lat_local = static_cast<size_t>(sb) * p.R + g * V + tid;
+      const size_t lat_local = static_cast<size_t>(sb) * p.R + g0 * V + tid;
       p.e_partial[lat_local * n_bands + band] = acc;
     }
   }

@@ -53,7 +53,9 @@ struct Bucket {
   int sweep_chunks = 0;       // blocks per lattice group in a half-sweep
   bool fused = false;         // sweeps use k_sweep_fused (ping-pong buffers)
   int band_rows = 0, n_bands = 0;  // fused-sweep tiling
-  size_t fused_smem = 0;      // dynamic shared memory of the fused sweep
+  int gp_or = 1, gp_hb = 1;   // fused sweep: lattice groups per CTA (each thread updates all)
+                              // of the overrelaxation and heat-bath kernels
+  size_t fused_smem = 0;      // dynamic shared memory of the larger of the two fused kernels
   double* d_epart = nullptr;  // [S_b*R][max(sweep_chunks, n_bands)]
   int m_chunks = 0, P = 0;
   bool m_warp = false;        // measurement: one warp per unit (small lattices)
@@ -95,7 +97,6 @@ struct hsg_ctx {
   uint32_t* d_counters = nullptr; // [0] HB sweeps, [1] PT sweeps
   float* d_stage = nullptr;     // staging for spins [max N][3]
   float* d_big = nullptr;       // staging for whole-sample transfers (grown on demand)
-  size_t fused_smem_attr = 0;   // dynamic shared memory the fused kernels are allowed
   size_t big_cap = 0;           // floats in d_big
   uint32_t* d_tmp_u32 = nullptr;
   bool energy_valid = false;
@@ -186,6 +187,24 @@ hsg_status dalloc(T** p, size_t n) {
 
 int acc_stride(const hsg_ctx* h) { return h->NT > 1 ? h->NT - 1 : 1; }
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit belongs to the kernel, not to a context: every
+// context of the process launches the same kernels, so the limit only ever
+// grows (a context needing less must not lower it under another context's
+// captured launches).
+hsg_status raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limits;
+  int dev = 0;
+  HSG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limits[{dev, fn}];
+  if (bytes <= cur) return HSG_OK;
+  HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+  cur = bytes;
+  return HSG_OK;
+}
+
 // Storage position of the natural site i = x + L*(y + L*z) (parity-split rows,
 // as on the device).
 size_t storage_site(size_t i, int L) {
@@ -234,19 +253,45 @@ hsg_status launch_half(hsg_ctx* h, const Bucket& b, int colour, bool energy, cud
 
 // The fused-sweep kernel for a tiling: compile-time specialisations for the
 // common ones (L = 64 and L = 32 in bands of 8 rows), the run-time-geometry
-// kernel otherwise.
+// kernel otherwise; gp lattice groups per CTA (2 only with two lattices per
+// element).
 using FusedKernel = void (*)(FusedParams);
 
-template <int KIND, int V, int PREC>
-FusedKernel fused_kernel(int L, int band_rows) {
-  if (L == 64 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 64, 8>;
-  if (L == 32 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 32, 8>;
-  return k_sweep_fused<KIND, V, PREC, 0, 0>;
+template <int KIND, int V, int PREC, int GP>
+FusedKernel fused_kernel_gp(int L, int band_rows) {
+  if (L == 64 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 64, 8, GP>;
+  if (L == 32 && band_rows == 8) return k_sweep_fused<KIND, V, PREC, 32, 8, GP>;
+  return k_sweep_fused<KIND, V, PREC, 0, 0, GP>;
 }
 
 template <int KIND, int V, int PREC>
-void fused_kernel_launch(const FusedParams& p, unsigned grid, unsigned block, size_t smem, cudaStream_t st) {
-  fused_kernel<KIND, V, PREC>(p.L, p.band_rows)<<<grid, block, smem, st>>>(p);
+FusedKernel fused_kernel(int L, int band_rows, int gp) {
+  if constexpr (V == 2) {
+    if (gp == 2) return fused_kernel_gp<KIND, V, PREC, 2>(L, band_rows);
+  }
+  return fused_kernel_gp<KIND, V, PREC, 1>(L, band_rows);
+}
+
+// Every fused kernel of (KIND, V, PREC) with gp groups per CTA.
+template <int KIND, int V, int PREC>
+std::vector<FusedKernel> fused_kernels(int gp) {
+  std::vector<FusedKernel> v;
+  for (const int L : {64, 32, 0}) v.push_back(fused_kernel<KIND, V, PREC>(L, L > 0 ? 8 : 0, gp));
+  return v;
+}
+
+template <int KIND, int V, int PREC>
+void fused_kernel_launch(const FusedParams& p, int gp, unsigned grid, unsigned block, size_t smem,
+                         cudaStream_t st) {
+  fused_kernel<KIND, V, PREC>(p.L, p.band_rows, gp)<<<grid, block, smem, st>>>(p);
+}
+
+// Dynamic shared memory of the fused kernel: a ring of kFusedSlots planes of
+// gp lattice groups, each the band plus two halo rows per side (or whole
+// planes), three components of L * V floats per row.
+size_t fused_smem_bytes(int L, int V, int gp, int band_rows) {
+  const int rows = (band_rows == L) ? L : band_rows + 4;
+  return static_cast<size_t>(kFusedSlots) * 3 * gp * rows * L * V * sizeof(float);
 }
 
 // One whole sweep (both colours) of a bucket with the fused kernel; reads the
@@ -278,10 +323,12 @@ hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, boo
   p.D = h->bimodal_D;
   const int rows_t = (b.band_rows == b.L) ? b.L : b.band_rows + 2;
   const unsigned block = static_cast<unsigned>(((rows_t * (b.L / 2)) + 31) / 32 * 32);
-  const unsigned grid = static_cast<unsigned>(b.S_b * b.G * b.n_bands);
+  const int gp = (KIND == kHB) ? b.gp_hb : b.gp_or;
+  const unsigned grid = static_cast<unsigned>(b.S_b * (b.G / gp) * b.n_bands);
+  const size_t smem = fused_smem_bytes(b.L, h->V, gp, b.band_rows);
   *h->launch_sink += 1;
   dispatch(h->V, h->prec, [&](auto v, auto pr) {
-    fused_kernel_launch<KIND, decltype(v)::value, decltype(pr)::value>(p, grid, block, b.fused_smem, st);
+    fused_kernel_launch<KIND, decltype(v)::value, decltype(pr)::value>(p, gp, grid, block, smem, st);
     return 0;
   });
   HSG_CUDA(cudaGetLastError());
@@ -291,19 +338,18 @@ hsg_status launch_fused(hsg_ctx* h, Bucket& b, bool energy, cudaStream_t st, boo
 
 template <int KIND, int V, int PREC>
 hsg_status allow_fused_smem(size_t bytes) {
-  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>,
-                         k_sweep_fused<KIND, V, PREC, 32, 8>})
-    HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+  for (const int gp : {1, 2})
+    for (FusedKernel fn : fused_kernels<KIND, V, PREC>(gp))
+      HSG_TRY(raise_smem_limit(reinterpret_cast<const void*>(fn), bytes));
   return HSG_OK;
 }
 
-// Smallest block limit over a kind's fused kernels, as the CUDA driver reports it
-// for their register use; 0 if unknown.
+// Smallest block limit over a kind's fused kernels with gp groups per CTA, as
+// the CUDA driver reports it for their register use; 0 if unknown.
 template <int KIND, int V, int PREC>
-int fused_max_threads_one() {
+int fused_max_threads_one(int gp) {
   int best = 1 << 30;
-  for (FusedKernel fn : {k_sweep_fused<KIND, V, PREC, 0, 0>, k_sweep_fused<KIND, V, PREC, 64, 8>,
-                         k_sweep_fused<KIND, V, PREC, 32, 8>}) {
+  for (FusedKernel fn : fused_kernels<KIND, V, PREC>(gp)) {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) {
       cudaGetLastError();
@@ -314,12 +360,13 @@ int fused_max_threads_one() {
   return best;
 }
 
-// Largest block the fused kernels (heat-bath and overrelaxation) can launch
-// with, as the CUDA driver reports it for their register use; 0 if unknown.
-int fused_max_threads(int V, int prec) {
-  return dispatch(V, prec, [](auto v, auto pr) {
+// Largest block the fused kernels (heat-bath and overrelaxation) with gp
+// groups per CTA can launch with, as the CUDA driver reports it for their
+// register use; 0 if unknown.
+int fused_max_threads(int V, int prec, int gp) {
+  return dispatch(V, prec, [gp](auto v, auto pr) {
     constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
-    const int a = fused_max_threads_one<kHB, VV, P>(), b = fused_max_threads_one<kOR, VV, P>();
+    const int a = fused_max_threads_one<kHB, VV, P>(gp), b = fused_max_threads_one<kOR, VV, P>(gp);
     return std::min(std::min(a, b), kFusedMaxThreads);
   });
 }
@@ -332,13 +379,17 @@ hsg_status allow_fused_smem_all(int V, int prec, size_t bytes) {
   });
 }
 
-// Tiling of the fused sweep for lattice size L and V lattices per element:
-// whole planes for L <= 24, else the smallest band of rows (a divisor of L,
-// at least 8) within the thread and shared-memory limits, else whole planes
-// if they fit.  False: use the two-pass half-sweep kernel.
-bool plan_fused(int L, int V, int max_threads, int want, int* band_rows, size_t* smem) {
+// Tiling of the fused sweep for lattice size L, V lattices per element and gp
+// lattice groups per CTA: whole planes for L <= 24, else the smallest band of
+// rows (a divisor of L, at least 8) within the thread and shared-memory
+// limits, else whole planes if they fit.  False: use the two-pass half-sweep
+// kernel.
+bool plan_fused(int L, int V, int gp, int max_threads, int want, int* band_rows, size_t* smem) {
   const size_t max_smem = 200 * 1024;
-  auto smem_for = [&](int rows) { return static_cast<size_t>(kFusedSlots) * 3 * rows * L * V * sizeof(float); };
+  auto smem_for = [&](int rows) {
+    return static_cast<size_t>(kFusedSlots) * 3 * gp * rows * L * V * sizeof(float);
+  };
+  if (gp != 1 && (gp != 2 || V != 2)) return false;
   // blocks are rounded up to whole warps
   auto threads_for = [&](int rows) { return (rows * (L / 2) + 31) / 32 * 32; };
   if (max_threads <= 0) return false;
@@ -475,7 +526,7 @@ hsg_status plan_persistent(hsg_ctx* h) {
         const size_t budget = static_cast<size_t>(optin) - fa.sharedSizeBytes;
         const size_t smem = spins + 3 * static_cast<size_t>(b.N) * bond_bytes[js];
         if (smem > budget) continue;
-        HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(budget)));
+        HSG_TRY(raise_smem_limit(fn, budget));
         int occ = 0;
         const int threads = persistent_threads(g_sub / gp, b.N / 2, fa.maxThreadsPerBlock);
         HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
@@ -775,6 +826,11 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   const long long R = static_cast<long long>(cfg->n_replicas) * cfg->n_temps;
   const int V = cfg->layout == HSG_LAYOUT_BATCHED ? 2 : 1;
   if (R % V != 0) return fail(HSG_EINVAL, "the batched layout needs an even number of lattices per sample");
+  if (cfg->fused_groups < 0 || cfg->fused_groups > 2 ||
+      (cfg->fused_groups > 0 && cfg->sweep_kernel != HSG_SWEEP_AUTO))
+    return fail(HSG_EINVAL, "fused_groups must be 0, or 1 or 2 with the fused sweep");
+  if (cfg->fused_groups == 2 && (V != 2 || R % 4 != 0))
+    return fail(HSG_EINVAL, "fused_groups = 2 needs the batched layout and a multiple of 4 lattices per sample");
   if (R * cfg->n_samples > 0x7fffffffLL) return fail(HSG_EINVAL, "too many lattices");
 
   hsg_ctx* h = new (std::nothrow) hsg_ctx();
@@ -834,10 +890,12 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     b.S_b = static_cast<int>(b.samples.size());
     b.G = h->R / V;
     b.sweep_chunks = (b.N / 2 + kSweepThreads - 1) / kSweepThreads;
+    b.gp_or = b.gp_hb = cfg->fused_groups > 0 ? cfg->fused_groups : 1;
     b.fused = (h->sweep_kernel == HSG_SWEEP_AUTO) &&
-              plan_fused(b.L, V, fused_max_threads(V, h->prec), cfg->band_rows, &b.band_rows, &b.fused_smem);
-    if (cfg->band_rows > 0 && !b.fused) {
-      fail(HSG_EINVAL, "band_rows does not tile L = " + std::to_string(b.L) + " within the limits");
+              plan_fused(b.L, V, b.gp_or, fused_max_threads(V, h->prec, b.gp_or), cfg->band_rows,
+                         &b.band_rows, &b.fused_smem);
+    if ((cfg->band_rows > 0 || cfg->fused_groups > 0) && !b.fused) {
+      fail(HSG_EINVAL, "band_rows / fused_groups do not tile L = " + std::to_string(b.L) + " within the limits");
       return bail(HSG_EINVAL);
     }
     b.n_bands = b.fused ? b.L / b.band_rows : 0;
@@ -895,7 +953,6 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   }
 
   if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
-  h->fused_smem_attr = max_fused_smem;
   if (h->persistent) {
     const hsg_status ps = plan_persistent(h);
     if (ps != HSG_OK) return bail(ps);
@@ -905,19 +962,12 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     size_t msmem = 0;
     for (const Bucket& b : h->buckets) msmem = std::max(msmem, measure_block_smem(b.L));
     if (msmem > 0) {
-      const cudaError_t e = dispatch(h->V, h->prec, [&](auto v, auto pr) {
+      const hsg_status e = dispatch(h->V, h->prec, [&](auto v, auto pr) {
         constexpr int VV = decltype(v)::value, P = decltype(pr)::value;
-        const cudaError_t a = cudaFuncSetAttribute(k_measure<VV, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(msmem));
-        return a != cudaSuccess ? a
-                                : cudaFuncSetAttribute(k_measure_warp<VV, P>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       static_cast<int>(msmem));
+        const hsg_status a = raise_smem_limit(reinterpret_cast<const void*>(k_measure<VV, P>), msmem);
+        return a != HSG_OK ? a : raise_smem_limit(reinterpret_cast<const void*>(k_measure_warp<VV, P>), msmem);
       });
-      if (e != cudaSuccess) {
-        fail(HSG_ECUDA, std::string("measurement shared memory: ") + cudaGetErrorString(e));
-        return bail(HSG_ECUDA);
-      }
+      if (e != HSG_OK) return bail(e);
     }
   }
   const size_t S = h->S, NT = h->NT;
@@ -1244,9 +1294,9 @@ hsg_status hsg_sweep_or_sequential(hsg_t h, int n) {
     smem_max = std::max(smem_max, smem);
   }
   if (n == 0) return HSG_OK;
-  HSG_CUDA((dispatch(h->V, h->prec, [&](auto v, auto pr) {
-    return cudaFuncSetAttribute(k_sweep_or_seq<decltype(v)::value, decltype(pr)::value>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_max));
+  HSG_TRY((dispatch(h->V, h->prec, [&](auto v, auto pr) {
+    return raise_smem_limit(reinterpret_cast<const void*>(k_sweep_or_seq<decltype(v)::value, decltype(pr)::value>),
+                            smem_max);
   })));
   for (const Bucket& b : h->buckets) {
     SeqParams p;
@@ -1410,13 +1460,15 @@ hsg_status hsg_get_counters(hsg_t h, uint64_t out[3]) {
   return HSG_OK;
 }
 
-hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[3]) {
+hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[5]) {
   if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   const Bucket& b = h->buckets[h->sample_bucket[sample]];
   out[0] = b.fused ? 1 : 0;
   out[1] = b.fused ? b.band_rows : 0;
   out[2] = b.fused ? 1 : 2;
+  out[3] = b.fused ? b.gp_or : 0;
+  out[4] = b.fused ? b.gp_hb : 0;
   return HSG_OK;
 }
 
@@ -1441,10 +1493,11 @@ hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]) {
 namespace {
 
 std::mutex g_tune_mu;
-// (kind, L, V, precision, N_T, bond residency) -> (band rows) or (gp, threads)
-std::map<std::array<int, 6>, std::array<int, 2>> g_tune_cache;
+// (kind, L, V, precision, N_T, bond residency) -> (band rows, overrelaxation
+// groups, heat-bath groups) or (gp, threads, 0)
+std::map<std::array<int, 6>, std::array<int, 3>> g_tune_cache;
 
-bool tune_lookup(const std::array<int, 6>& key, std::array<int, 2>* val) {
+bool tune_lookup(const std::array<int, 6>& key, std::array<int, 3>* val) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const auto it = g_tune_cache.find(key);
   if (it == g_tune_cache.end()) return false;
@@ -1452,7 +1505,7 @@ bool tune_lookup(const std::array<int, 6>& key, std::array<int, 2>* val) {
   return true;
 }
 
-void tune_store(const std::array<int, 6>& key, const std::array<int, 2>& val) {
+void tune_store(const std::array<int, 6>& key, const std::array<int, 3>& val) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = val;
 }
@@ -1478,58 +1531,42 @@ hsg_status time_ms(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1, int reps, F&& lau
 // CTAs to fill the GPU (few small lattices).
 hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
   const std::array<int, 6> key = {0, b.L, h->V, h->prec, b.S_b * h->R, 0};
-  std::array<int, 2> got;
-  std::vector<int> cands;
-  if (tune_lookup(key, &got)) {
-    cands.push_back(got[0]);
-  } else {
-    cands.push_back(b.band_rows);  // the current plan first: ties keep it
-    for (int B = 8; B <= b.L; ++B)
-      if (b.L % B == 0 && B != b.band_rows) cands.push_back(B);
-    cands.push_back(0);
-  }
-  const int mt = fused_max_threads(h->V, h->prec);
-  int best_band = b.band_rows;
-  size_t best_smem = b.fused_smem;
-  float best_ms = -1.0f;
-  for (const int want : cands) {
-    if (want == 0) {  // the two-pass half-sweeps
-      if (cands.size() == 1) {
-        best_band = 0;
-        break;
-      }
-      const size_t bytes = sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
-      HSG_CUDA(cudaMemcpyAsync(b.d_spins[b.cur ^ 1], b.d_spins[b.cur], bytes, cudaMemcpyDeviceToDevice,
-                               h->stream));
-      b.cur ^= 1;
-      float ms = 0.0f;
-      const hsg_status st = time_ms(h, e0, e1, 3, [&]() -> hsg_status {
-        HSG_TRY(launch_half<kOR>(h, b, 0, false, h->stream));
-        return launch_half<kOR>(h, b, 1, false, h->stream);
-      }, &ms);
-      b.cur ^= 1;
-      HSG_TRY(st);
-      if (best_ms < 0.0f || ms < 0.98f * best_ms) {
-        best_ms = ms;
-        best_band = 0;
-      }
-      continue;
+  std::array<int, 3> got;
+  const bool remembered = tune_lookup(key, &got);
+  // two lattice groups per CTA need the batched layout and whole group pairs
+  const bool two_groups = (h->V == 2 && h->R % 4 == 0);
+  auto set_plan = [&](int band, int gp_or, int gp_hb) -> hsg_status {
+    b.band_rows = band;
+    b.n_bands = b.L / band;
+    b.gp_or = gp_or;
+    b.gp_hb = gp_hb;
+    b.fused_smem = std::max(fused_smem_bytes(b.L, h->V, gp_or, band), fused_smem_bytes(b.L, h->V, gp_hb, band));
+    return allow_fused_smem_all(h->V, h->prec, b.fused_smem);
+  };
+  if (remembered) {  // nothing to time
+    if (got[0] == 0) {
+      b.fused = false;
+      return HSG_OK;
     }
+    return set_plan(got[0], got[1], got[2]);
+  }
+  // The overrelaxation sweep (n_or of them per step) decides the band height
+  // and the two-pass alternative; candidates (band rows, groups per CTA),
+  // the current plan first so that ties keep it.
+  std::vector<std::array<int, 2>> cands;
+  cands.push_back({b.band_rows, b.gp_or});
+  for (const int gp : {1, 2}) {
+    if (gp == 2 && !two_groups) continue;
+    for (int B = 8; B <= b.L; ++B)
+      if (b.L % B == 0 && !(B == b.band_rows && gp == b.gp_or)) cands.push_back({B, gp});
+  }
+  int best_band = b.band_rows, best_gp = b.gp_or;
+  float best_ms = -1.0f;
+  for (const auto& cand : cands) {
     int br = 0;
     size_t sm = 0;
-    if (!plan_fused(b.L, h->V, mt, want, &br, &sm)) continue;
-    if (sm > h->fused_smem_attr) {
-      if (allow_fused_smem_all(h->V, h->prec, sm) != HSG_OK) return HSG_ECUDA;
-      h->fused_smem_attr = sm;
-    }
-    b.band_rows = br;
-    b.n_bands = b.L / br;
-    b.fused_smem = sm;
-    if (cands.size() == 1) {  // remembered choice: nothing to time
-      best_band = br;
-      best_smem = sm;
-      break;
-    }
+    if (!plan_fused(b.L, h->V, cand[1], fused_max_threads(h->V, h->prec, cand[1]), cand[0], &br, &sm)) continue;
+    HSG_TRY(set_plan(br, cand[1], b.gp_hb));
     float ms = 0.0f;
     HSG_TRY(time_ms(h, e0, e1, 3, [&]() -> hsg_status {
       HSG_TRY(launch_fused<kOR>(h, b, false, h->stream));
@@ -1540,17 +1577,49 @@ hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
     if (best_ms < 0.0f || ms < 0.98f * best_ms) {
       best_ms = ms;
       best_band = br;
-      best_smem = sm;
+      best_gp = cand[1];
     }
   }
-  if (best_band == 0) {
-    b.fused = false;  // the state stays in the current buffer
-  } else {
-    b.band_rows = best_band;
-    b.n_bands = b.L / best_band;
-    b.fused_smem = best_smem;
+  {  // the two-pass half-sweeps, timed on a copy of the state in the other buffer
+    const size_t bytes = sizeof(float) * static_cast<size_t>(b.S_b) * h->R * 3 * b.N;
+    HSG_CUDA(cudaMemcpyAsync(b.d_spins[b.cur ^ 1], b.d_spins[b.cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    b.cur ^= 1;
+    float ms = 0.0f;
+    const hsg_status st = time_ms(h, e0, e1, 3, [&]() -> hsg_status {
+      HSG_TRY(launch_half<kOR>(h, b, 0, false, h->stream));
+      return launch_half<kOR>(h, b, 1, false, h->stream);
+    }, &ms);
+    b.cur ^= 1;
+    HSG_TRY(st);
+    if (best_ms < 0.0f || ms < 0.98f * best_ms) {
+      b.fused = false;  // the state stays in the current buffer
+      tune_store(key, {0, 1, 1});
+      return HSG_OK;
+    }
   }
-  tune_store(key, {best_band, 0});
+  // The heat-bath sweep keeps the band and picks its own groups per CTA.
+  int best_hb = b.gp_hb;
+  if (two_groups) {
+    float hb_ms = -1.0f;
+    for (const int gp : {b.gp_hb, 3 - b.gp_hb}) {
+      int br = 0;
+      size_t sm = 0;
+      if (!plan_fused(b.L, h->V, gp, fused_max_threads(h->V, h->prec, gp), best_band, &br, &sm)) continue;
+      HSG_TRY(set_plan(best_band, best_gp, gp));
+      float ms = 0.0f;
+      HSG_TRY(time_ms(h, e0, e1, 3, [&]() -> hsg_status {
+        HSG_TRY(launch_fused<kHB>(h, b, false, h->stream));
+        b.cur ^= 1;
+        return HSG_OK;
+      }, &ms));
+      if (hb_ms < 0.0f || ms < 0.98f * hb_ms) {
+        hb_ms = ms;
+        best_hb = gp;
+      }
+    }
+  }
+  HSG_TRY(set_plan(best_band, best_gp, best_hb));
+  tune_store(key, {best_band, best_gp, best_hb});
   return HSG_OK;
 }
 
@@ -1559,7 +1628,7 @@ hsg_status tune_fused(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
 // energies, acceptances), so the context's state is untouched.
 hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1) {
   const std::array<int, 6> key = {1, b.L, h->V, h->prec, h->NT * 256 + b.res_gsub, b.res_js};
-  std::array<int, 2> got;
+  std::array<int, 3> got;
   if (tune_lookup(key, &got)) {
     b.res_gp = got[0];
     b.res_threads = got[1];
@@ -1606,8 +1675,7 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
       cudaFuncAttributes fa;
       HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
       if (c[1] > fa.maxThreadsPerBlock) continue;
-      HSG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - static_cast<int>(fa.sharedSizeBytes)));
+      HSG_TRY(raise_smem_limit(fn, static_cast<size_t>(optin) - fa.sharedSizeBytes));
       int occ = 0;
       HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c[1], b.res_smem));
       if (occ < 1) continue;
@@ -1621,7 +1689,7 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
     }
     b.res_gp = best_gp;
     b.res_threads = best_threads;
-    tune_store(key, {best_gp, best_threads});
+    tune_store(key, {best_gp, best_threads, 0});
     return HSG_OK;
   };
   if (st == HSG_OK) st = run();

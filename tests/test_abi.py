@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 25
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.hsg_version() == hsg.ABI_VERSION == 2
+    assert lib.hsg_version() == hsg.ABI_VERSION == 3
 
 
 def _cfg(**kw):

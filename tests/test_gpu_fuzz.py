@@ -109,6 +109,48 @@ def test_every_fused_tiling_equals_the_two_pass_sweep(L, band):
     b.destroy()
 
 
+def _ring_bytes(L, band, gp):
+    """Shared memory of the fused sweep's ring with gp lattice groups of two
+    lattices per element."""
+    rows = L if band == L else band + 4
+    return 4 * 3 * gp * rows * L * 2 * 4
+
+
+TILINGS_GP2 = [(L, B) for L, B in TILINGS if _ring_bytes(L, B, 2) <= 200 * 1024
+               and (L if B == L else B + 2) * (L // 2) <= 384]
+
+
+@pytest.mark.parametrize("L,band", TILINGS_GP2, ids=[f"L{L}_b{B}" for L, B in TILINGS_GP2])
+def test_two_groups_per_thread_equal_the_two_pass_sweep(L, band):
+    """Two lattice groups per thread (each coupling loaded and converted once
+    for four lattices), at each band height whose ring fits: the two-pass
+    kernel's spins bit for bit over heat-bath and overrelaxation sweeps, the
+    same labels and acceptances, and the energies of one group per thread in
+    the same bands exactly (the same partial sums in the same order)."""
+    c = dict(Ls=[L, L], betas=[0.7, 1.9], n_rep=2, layout=hsg.BATCHED, prec=hsg.F16, n_or=2, me=0)
+    a = _make(c, band_rows=band, fused_groups=2)
+    plan = a.get_sweep_plan(0)
+    assert plan["fused"] and plan["band_rows"] == band
+    assert plan["groups_per_thread_or"] == 2 and plan["groups_per_thread_hb"] == 2
+    b = _make(c, sweep_kernel=hsg.SWEEP_TWO_PASS)
+    one = _make(c, band_rows=band, fused_groups=1)
+    ra, rb, r1 = _result(a, 2), _result(b, 2), _result(one, 2)
+    assert all(np.array_equal(x, y) for rx, ry in zip(ra[0], rb[0]) for x, y in zip(rx, ry))
+    assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[2], rb[2])
+    assert np.array_equal(ra[3], r1[3])
+    for lat in (a, b, one):
+        lat.destroy()
+
+
+def test_two_groups_per_thread_needs_whole_group_pairs():
+    """fused_groups = 2 with 2 lattices per sample, or the plain layout, is
+    refused before anything is allocated."""
+    with pytest.raises(hsg.HsgError, match="fused_groups"):
+        hsg.Lattice(16, [0.5, 1.0], n_replicas=1, coupling_prec=hsg.F16, layout=hsg.BATCHED, fused_groups=2)
+    with pytest.raises(hsg.HsgError, match="fused_groups"):
+        hsg.Lattice(16, [0.5, 1.0], n_replicas=2, coupling_prec=hsg.F16, layout=hsg.PLAIN, fused_groups=2)
+
+
 RESIDENT = [(L, layout, NT) for L in (4, 6, 8, 10, 12, 14, 16, 18, 20)
             for layout in (hsg.PLAIN, hsg.BATCHED) for NT in (2, 16)]
 

@@ -352,3 +352,35 @@ def test_per_half_sweep_parity_across_sizes(L, prec, layout):
         assert d <= SWEEP_TOL and du <= SWEEP_TOL, (kind, d, du)
         assert amb <= max(3, 1e-3 * lat.R * L ** 3)
     lat.destroy()
+
+
+def test_a_smaller_context_does_not_shrink_another_contexts_limits():
+    """Kernel shared-memory limits belong to the kernels, which every context
+    shares: creating a context that needs less (smaller rings, smaller
+    measurement tables) after one that needs more must leave the first
+    runnable.  Both then run whole measured steps and match one context
+    alone bit for bit."""
+    big = dict(Ls=[32], betas=[0.6, 1.3], n_rep=2)
+    small = dict(Ls=[8], betas=[0.6, 1.3], n_rep=2)
+
+    def make_ctx(c, **kw):
+        lat = hsg.Lattice(c["Ls"], c["betas"], n_replicas=c["n_rep"], coupling_prec=hsg.F16,
+                          layout=hsg.BATCHED, n_or=2, measure_every=1, seed=3, **kw)
+        for s, L in enumerate(c["Ls"]):
+            lat.set_couplings(s, gi.couplings(L, 3, s, precision="f16"))
+            lat.set_spins_sample(s, gi.random_spins_batch(L, 3, s, lat.R))
+        return lat
+
+    alone = make_ctx(big, band_rows=8, fused_groups=2)
+    alone.run_steps(2)
+    ref = state(alone), alone.read_observables()[0].copy()
+    alone.destroy()
+    a = make_ctx(big, band_rows=8, fused_groups=2)     # the larger fused ring and measurement table
+    b = make_ctx(small, band_rows=8, fused_groups=1)   # created after, needing less of both
+    b.run_steps(2)
+    a.run_steps(2)
+    got = state(a), a.read_observables()[0].copy()
+    assert all(np.array_equal(x, y) for rx, ry in zip(ref[0], got[0]) for x, y in zip(rx, ry))
+    assert np.array_equal(ref[1], got[1])
+    a.destroy()
+    b.destroy()
