@@ -329,16 +329,21 @@ hsg_status hsg_philox4x32_10(const uint32_t *in, long n, uint32_t *out);
  *   E_out  device double [n_samples*lattices_per_sample], receives
  *          E = -sum_bonds s_x^T J s_y (FP32 terms, FP64 sums);
  *   stream cudaStream_t to run on (NULL = legacy default stream).
- * All three buffers belong to the caller.  The work is enqueued
+ * All three buffers belong to the caller.  Before anything is launched each
+ * is checked to be device (or managed) memory usable by the current device,
+ * inside one allocation large enough for the sizes given, and aligned (spins
+ * 4 bytes, J6 and E_out 8 bytes); HSG_EINVAL otherwise.  The work is enqueued
  * asynchronously.  The only working memory is a fixed device array of
  * HSG_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) inside the library, which every
  * GPU that loads the library holds until the process exits; a request needing
  * more than that (lattices x ceil(L^3/512) partial sums) is rejected with
- * HSG_EINVAL before anything runs.  The first call on each device looks up
- * the array's device address with that device current; make that first call
- * before any stream capture.  All calls on a device share the array and it
- * keeps the last call's contents (each call writes every entry it reads, so
- * nothing needs clearing), so calls that overlap on the GPU race and give
+ * HSG_EINVAL before anything runs.  The first call in each CUDA context (per
+ * device, and again after the context is destroyed and re-created) looks up
+ * the array's device address with that context current; make that first call
+ * before any stream capture (a first call on a capturing stream returns
+ * HSG_ESTATE and enqueues nothing).  All calls on a device share the array and
+ * it keeps the last call's contents (each call writes every entry it reads,
+ * so nothing needs clearing), so calls that overlap on the GPU race and give
  * wrong results: order them on one stream. */
 #define HSG_NOALLOC_SCRATCH_DOUBLES 262144
 hsg_status hsg_energy_noalloc(const float *spins, const float *J6, int L, int n_samples,
