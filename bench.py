@@ -36,11 +36,27 @@ METRIC = "spin updates/ns and % HBM roofline, batched FP16-coupling vs plain FP3
 UNIT = "spin updates/ns"
 MCS_PER_STEP = 10
 
+# Coupling storage ("prec": "f16" unless given) and spin layout ("layout":
+# "batched", two lattices per element, unless given) of each workload.
 WORKLOADS = {
     "L64_S8_R64_f16": dict(L=64, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
+    # the plain method at L=8: one sample, 2 replicas at T = 0.5, FP32
+    # couplings, one lattice per element, observables every step (no PT)
+    "L8_S1_R2_f32": dict(L=8, S=1, n_rep=2, NT=1, Tmin=0.5, Tmax=0.5, n_or=8, measure_every=1,
+                         prec="f32", layout="plain"),
+    # one L=16 sample with PT over 16 temperatures in [0.15, 0.75] x 2
+    # replicas, FP32 couplings, observables every 10 steps
+    "L16_S1_R32_f32": dict(L=16, S=1, n_rep=2, NT=16, Tmin=0.15, Tmax=0.75, n_or=8,
+                           measure_every=10, prec="f32"),
     "L32_S64_R48_f16": dict(L=32, S=64, n_rep=2, NT=24, Tmin=0.15, Tmax=0.75, n_or=8,
                             measure_every=10),
+    # the plain single-lattice form at L=64: 512 samples of one lattice each at
+    # T = 0.5, FP32 couplings of their own (no two lattices share a coupling
+    # read), one lattice per element; the default run builds it from its own
+    # inputs (each lattice with its own copy of its sample's couplings)
+    "L64_S512_R1_f32_plain": dict(L=64, S=512, n_rep=1, NT=1, Tmin=0.5, Tmax=0.5, n_or=8, measure_every=10,
+                                  prec="f32", layout="plain"),
     # profiling size: 512 lattices of L=32 (201 MB of spins, above L2)
     "L32_S8_R64_f16": dict(L=32, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
@@ -57,6 +73,8 @@ WORKLOADS = {
                              measure_every=10, persistent=True),
 }
 DEFAULT_WORKLOAD = "L64_S8_R64_f16"
+# the plain single-lattice form timed beside the default workload
+SINGLE_WORKLOAD = "L64_S512_R1_f32_plain"
 # the small- and mid-size-lattice workloads summarised in every run of another workload
 SMALL_WORKLOAD = "L8x256_L12x256_R32_f16"
 MID_WORKLOAD = "L16_S512_R32_f16"
@@ -67,11 +85,17 @@ MID_WORKLOAD = "L16_S512_R32_f16"
 FUSED_SOURCES = ("kernels.cuh", "fused.cuh", "philox.cuh")
 RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
-    # profiles/k_sweep_fused_or_L64_S1_R64_f16.md: 387.3 MB for one sample, x8 samples
-    ("7ae4e3bdae527860", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3098738688,
-    # profiles/k_sweep_fused_or_L32_S64_R48_f16.md: one launch of the bench's workload
-    ("7ae4e3bdae527860", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645332736,
-    # profiles/k_persistent_L8x256_L12x256_R32_f16.md: both launches of 10 MCS
+    # the L=64 overrelaxation sweep in 8-row bands: 388.0 MB for one sample of
+    # 64 lattices, x8 samples
+    ("f337c22e34aed967", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3103889408,
+    # the same sweep of the plain FP32 form (one lattice per element): 418.4 MB
+    # for one sample, x8 samples; the 64 lattices of a sample read their
+    # shared couplings through L2, so this is far below the 96 B per update
+    # that lattices with couplings of their own move
+    ("f337c22e34aed967", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
+    # the L=32 overrelaxation sweep: one launch of 64 samples x 48 lattices
+    ("f337c22e34aed967", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
+    # the resident steps of 256 x L=8 + 256 x L=12 samples: both launches of 10 MCS
     ("a08c3f36068e5e63", "L8x256_L12x256_R32_f16",
      "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361512192,
 }
@@ -80,6 +104,17 @@ NCU_TRAFFIC = {
 def sample_Ls(w):
     """Linear size of each sample of the workload."""
     return list(w["Ls"]) if "Ls" in w else [w["L"]] * w["S"]
+
+
+def workload_form(hsg, w):
+    """(coupling storage, spin layout) of the workload's own form."""
+    prec = {"f16": hsg.F16, "f32": hsg.F32}[w.get("prec", "f16")]
+    layout = hsg.PLAIN if w.get("layout") == "plain" else hsg.BATCHED
+    return prec, layout
+
+
+def spin_bytes(w):
+    return 12 * w["n_rep"] * w["NT"] * sum(L ** 3 for L in sample_Ls(w))
 
 
 def kernel_source_hash(files=FUSED_SOURCES) -> str:
@@ -167,10 +202,21 @@ def make_inputs(w, rank, seed=1, n_samples=None):
     import hsg_inputs as gi
     Ls, S, R = sample_Ls(w), w["S"], w["n_rep"] * w["NT"]
     samples = [rank * S + s for s in range(S if n_samples is None else min(S, n_samples))]
-    J = [gi.couplings(Ls[s], seed, sg, precision="f16") for s, sg in enumerate(samples)]
+    J = [gi.couplings(Ls[s], seed, sg, precision=w.get("prec", "f16")) for s, sg in enumerate(samples)]
     spins = [[gi.random_spins(Ls[s], seed, sg, j) for j in range(R)] for s, sg in enumerate(samples)]
     beta = gi.linear_betas(w["Tmin"], w["Tmax"], w["NT"])
     return samples, J, spins, beta
+
+
+def single_lattice_inputs(inputs):
+    """The default workload's lattices as samples of one lattice each (at
+    T = 0.5), each given its own device copy of its sample's couplings: the
+    same values, but every lattice reads its couplings from an address of its
+    own, as lattices with distinct couplings do."""
+    samples, J, spins, beta = inputs
+    flat = [(s, j) for s in range(len(samples)) for j in range(len(spins[s]))]
+    return (list(range(len(flat))), [J[s] for s, _ in flat], [[spins[s][j]] for s, j in flat],
+            np.array([1.0 / 0.5]))
 
 
 # ----------------------------------------------------------------------------
@@ -238,19 +284,20 @@ def philox_key(rank: int) -> int:
 
 
 def build_lattice(hsg, w, samples, J, spins, beta, prec, layout, seed=1, band_rows=0,
-                  persistent=False, key=1):
+                  persistent=False, key=1, fused_groups=0):
     import hsg_inputs as gi
     Ls = sample_Ls(w)
     lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=prec,
                       layout=layout, n_or=w["n_or"], measure_every=w["measure_every"], seed=key,
-                      band_rows=band_rows, persistent=persistent, bimodal_D=BIMODAL_D)
+                      band_rows=band_rows, persistent=persistent, bimodal_D=BIMODAL_D,
+                      fused_groups=fused_groups)
     for s in range(len(samples)):
         if prec == hsg.BIMODAL:
             lat.set_couplings_bimodal(s, gi.bimodal_bits(Ls[s], seed, samples[s]))
         else:
             lat.set_couplings(s, J[s])
         lat.set_spins_sample(s, np.stack(spins[s]))
-    if band_rows == 0:
+    if band_rows == 0 and fused_groups == 0:
         lat.autotune()                 # launch shapes timed on this data, outside any timed region
     return lat
 
@@ -344,11 +391,11 @@ def time_sequential_or(hsg, w, inputs, torch, n_calls=3):
 
 
 def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampler, peak, band_rows=0,
-             persistent=False):
+             persistent=False, fused_groups=0):
     w = WORKLOADS[wname]
     samples, J, spins, beta = inputs
     lat = build_lattice(hsg, w, samples, J, spins, beta, prec, layout, band_rows=band_rows,
-                        persistent=persistent, key=philox_key(dist.rank))
+                        persistent=persistent, key=philox_key(dist.rank), fused_groups=fused_groups)
     R = lat.R
     n_sites = sum(L ** 3 for L in sample_Ls(w))
     # the autotuned launch shapes, one entry per lattice size
@@ -397,7 +444,8 @@ def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampl
     achieved = bytes_launch / (or_ms * 1e-3) / 1e9
     vname = 2 if layout == hsg.BATCHED else 1
     pname = {hsg.F16: "f16", hsg.F32: "f32", hsg.BIMODAL: "bimodal"}[prec]
-    kname = (f"k_sweep_fused<OR,{vname},{pname}> (bands of {plan['band_rows']} rows)" if plan["fused"]
+    gps = ", 2 lattice groups per thread" if plan.get("groups_per_thread_or", 1) == 2 else ""
+    kname = (f"k_sweep_fused<OR,{vname},{pname}> (bands of {plan['band_rows']} rows{gps})" if plan["fused"]
              else f"k_sweep_half<OR,{vname},{pname}>")
     roof = {"bound": "hbm", "kernel": kname,
             "achieved": round(achieved, 1), "peak": peak[0], "peak_source": peak[1],
@@ -421,8 +469,9 @@ def e2e_run(hsg, torch, dist, w, inputs, steps):
     device->host.  Wall time around it, synchronised."""
     samples, J, spins, beta = inputs
     Ls, S = sample_Ls(w), len(samples)
-    lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=hsg.F16,
-                      layout=hsg.BATCHED, n_or=w["n_or"], measure_every=w["measure_every"],
+    prec, layout = workload_form(hsg, w)
+    lat = hsg.Lattice(Ls, beta, n_replicas=w["n_rep"], coupling_prec=prec,
+                      layout=layout, n_or=w["n_or"], measure_every=w["measure_every"],
                       persistent=w.get("persistent", False), seed=philox_key(dist.rank))
     R, n_sites = lat.R, sum(L ** 3 for L in Ls)
     lat.autotune()                     # the shapes tuned for this workload (remembered)
@@ -478,10 +527,76 @@ def cpu_baseline(w, inputs, budget_s=15.0):
         more = max(1, int(n * (budget_s / max(dt, 1e-3) - 1)))
         u2, d2 = oracle_sample_run(w, inputs, more, threads)
         ups, dt, n = ups + u2, dt + d2, n + more
+    cq = "FP16-quantised" if w.get("prec", "f16") == "f16" else "FP32"
     return {"value": ups / (dt * 1e9), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} MCS of 1 sample ({w['n_rep'] * w['NT']} lattices of L={sample_Ls(w)[0]}, "
-                      f"FP16-quantised couplings as FP64), OpenMP over lattices, "
+                      f"{cq} couplings as FP64), OpenMP over lattices, "
                       f"{dt:.1f} s"}
+
+
+def oracle_error(hsg, w, inputs):
+    """Error of the GPU form against the FP64 oracle on sample 0 of the
+    workload (the couplings as stored, the oracle computing in FP64 on the
+    identical values), per stage:
+      * one overrelaxation sweep from an identical state: the largest spin
+        difference over four sampled lattices (trajectories under identical
+        streams separate only over many sweeps, so this is the per-sweep
+        arithmetic error);
+      * after one Monte Carlo step, the fused energies against the oracle's
+        energy of the same spins, and one measurement of every observable
+        against the oracle's measurement of the same spins and labels: the
+        largest difference over the temperatures relative to the largest
+        magnitude of that observable.
+    Part of the CPU-baseline leg (the oracle on the timed sample).  The
+    long-run averages are compared statistically by the GPU test suite."""
+    import oracle
+    samples, J, spins, beta = inputs
+    L = sample_Ls(w)[0]
+    N, NT, n_rep = L ** 3, w["NT"], w["n_rep"]
+    prec, layout = workload_form(hsg, w)
+    lat = hsg.Lattice([L], beta, n_replicas=n_rep, coupling_prec=prec, layout=layout,
+                      n_or=w["n_or"], measure_every=0, seed=1)
+    lat.set_couplings(0, J[0])
+    lat.set_spins_sample(0, np.stack(spins[0]))
+    J9 = oracle.j9_from_j6(J[0])
+    R = lat.R
+    before = lat.get_spins_sample(0).astype(np.float64)
+    lat.sweep_or(1)
+    after = lat.get_spins_sample(0)
+    ds = 0.0
+    for j in sorted({0, 1, R // 2, R - 1}):
+        ref = np.ascontiguousarray(before[j])
+        oracle.sweep(L, J9, ref, oracle.OR)
+        ds = max(ds, float(np.abs(after[j] - ref).max()))
+    lat.run_steps(1)
+    lat.reset_observables()
+    lat.measure()
+    obs, _ = lat.read_observables()
+    E, perm = lat.get_energies(), lat.get_perm()
+    st = lat.get_spins_sample(0).astype(np.float64)
+    lat.destroy()
+    ref = np.zeros((NT, hsg.NOBS))
+    e_err = 0.0
+    for k in range(NT):
+        for r in range(n_rep):
+            slot = perm[0, r, k]
+            e = oracle.energy(L, J9, st[slot])
+            e_err = max(e_err, abs(E[0, slot] - e) / abs(e))
+            ref[k, 0] += e / N
+            ref[k, 1] += (e / N) ** 2
+            ref[k, 8] += oracle.sd_residual(L, J9, st[slot], 1 / beta[k])
+        for pr in range(n_rep // 2):
+            ref[k, 2:8] += oracle.measure_pair(L, st[perm[0, 2 * pr, k]], st[perm[0, 2 * pr + 1, k]])
+    rel = {}
+    for j, name in enumerate(oracle.OBS_NAMES):
+        scale = float(np.abs(ref[:, j]).max())
+        if j >= 2 and j < 8 and n_rep < 2:
+            continue
+        rel[name] = float(f"{np.abs(obs[0, :, j] - ref[:, j]).max() / scale:.3g}") if scale > 0 else None
+    return {"sample": f"sample 0 ({R} lattices of L={L}, {w.get('prec', 'f16').upper()} couplings)",
+            "or_sweep_max_abs_ds": float(f"{ds:.3g}"),
+            "energy_max_rel_diff": float(f"{e_err:.3g}"),
+            "measurement_max_rel_diff": rel}
 
 
 def workload_config(name, w, world):
@@ -492,11 +607,15 @@ def workload_config(name, w, world):
             "samples_per_gpu": w["S"],
             "lattices_per_sample": w["n_rep"] * w["NT"], "n_temps": w["NT"],
             "T_range": [w["Tmin"], w["Tmax"]], "n_or": w["n_or"],
-            "couplings": "gaussian, FP16-quantised", "layout": "batched",
+            "couplings": ("gaussian, FP16-quantised" if w.get("prec", "f16") == "f16" else
+                          "gaussian, FP32"),
+            "layout": w.get("layout", "batched"),
             "step": f"{MCS_PER_STEP} MCS (HB + {w['n_or']} OR + PT each) + 1 measurement",
-            "l2": ("no flush: spins per GPU exceed L2 (126 MB)" if not persistent else
-                   "no flush: spins stay in shared memory within a launch; "
-                   "the whole set (220 MB per GPU) exceeds L2"),
+            "l2": ("no flush: spins stay in shared memory within a launch; "
+                   f"the whole set ({spin_bytes(w) / 1e6:.0f} MB per GPU) exceeds L2" if persistent else
+                   "no flush: spins per GPU exceed L2 (126 MB)" if spin_bytes(w) > 126e6 else
+                   f"no flush: the whole state ({spin_bytes(w) / 1e3:.0f} KB of spins) stays in L2 in any "
+                   "run of this size; the workload is latency-bound and not graded against HBM"),
             "resident": persistent,
             "parallelism": f"replicas x{world} (independent samples per GPU)"}
 
@@ -542,6 +661,8 @@ def main():
                     help="skip the summary of the small-lattice workload (resident steps)")
     ap.add_argument("--band-rows", type=int, default=0,
                     help="rows per CTA band of the fused sweep (0: library choice)")
+    ap.add_argument("--fused-groups", type=int, default=0,
+                    help="lattice groups per thread of the fused sweeps (0: library choice)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     world, rank, local = dist_env()
@@ -557,8 +678,13 @@ def main():
 
     sampler = ClockSampler(local)
     persistent = w.get("persistent", False)
-    batched = run_form(hsg, torch, dist, args.workload, inputs, hsg.F16, hsg.BATCHED, args.steps,
-                       args.warmup, sampler, peak, band_rows=args.band_rows, persistent=persistent)
+    wprec, wlayout = workload_form(hsg, w)
+    # the plain FP32 and bimodal comparisons and the small- and mid-lattice
+    # summaries go with the streaming FP16 batched workloads
+    f16_streaming = (wprec == hsg.F16 and wlayout == hsg.BATCHED and not persistent)
+    batched = run_form(hsg, torch, dist, args.workload, inputs, wprec, wlayout, args.steps,
+                       args.warmup, sampler, peak, band_rows=args.band_rows, persistent=persistent,
+                       fused_groups=args.fused_groups)
     if batched["lat"] is not None:
         batched["lat"].destroy()
     streaming = None
@@ -569,13 +695,17 @@ def main():
         streaming = run_form(hsg, torch, dist, args.workload, inputs, hsg.F16, hsg.BATCHED, args.steps,
                              args.warmup, None, peak)
         streaming["lat"].destroy()
-    plain = None
-    if not args.no_plain and not persistent:
+    plain = single = None
+    if not args.no_plain and f16_streaming:
         plain = run_form(hsg, torch, dist, args.workload, inputs, hsg.F32, hsg.PLAIN, args.steps,
                          args.warmup, None, peak)
         plain["lat"].destroy()
+        if args.workload == DEFAULT_WORKLOAD:
+            single = run_form(hsg, torch, dist, SINGLE_WORKLOAD, single_lattice_inputs(inputs), hsg.F32,
+                              hsg.PLAIN, args.steps, args.warmup, None, peak)
+            single["lat"].destroy()
     bimodal = {}
-    if not args.no_bimodal and not persistent:
+    if not args.no_bimodal and f16_streaming:
         for key, layout in (("bimodal_plain", hsg.PLAIN), ("bimodal_batched", hsg.BATCHED)):
             r = run_form(hsg, torch, dist, args.workload, inputs, hsg.BIMODAL, layout, args.steps, args.warmup,
                          None, peak)
@@ -583,7 +713,7 @@ def main():
             bimodal[key] = {"value": round(r["value"], 3), "ms_per_step": round(r["ms_per_step"], 3),
                             "D": BIMODAL_D, "roofline": r["roofline"], "gpu_launches": r["launches"]}
     small = mid = None
-    if not args.no_small and not persistent:
+    if not args.no_small and f16_streaming:
         # many small lattices: resident steps against the streaming kernels,
         # and the sequential overrelaxation sweep, on the same inputs
         ws = WORKLOADS[SMALL_WORKLOAD]
@@ -616,9 +746,10 @@ def main():
                "resident_over_streaming": round(res["value"] / strm["value"], 3)}
         del inputs_m
     e2e = None if args.no_e2e else e2e_run(hsg, torch, dist, w, inputs, args.steps)
-    cpu = None
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, inputs)
+        err = oracle_error(hsg, w, inputs)
     if rank == 0:
         line = {"metric": METRIC, "value": round(batched["value"], 3), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -627,11 +758,23 @@ def main():
                 "config": workload_config(args.workload, w, world),
                 "roofline": batched["roofline"], "gpu_launches": batched["launches"],
                 "clocks": batched["clocks"], "e2e": e2e, "cpu_baseline": cpu}
+        if err is not None:
+            line["oracle_error"] = err
         if plain is not None:
             line["plain_fp32"] = {"value": round(plain["value"], 3),
                                   "ms_per_step": round(plain["ms_per_step"], 3),
-                                  "roofline": plain["roofline"], "gpu_launches": plain["launches"]}
+                                  "roofline": plain["roofline"], "gpu_launches": plain["launches"],
+                                  "note": "one lattice per element, but the lattices of a sample share "
+                                          "their couplings through L2 (traffic well below the algorithmic "
+                                          "96 B per update), so frac is not an HBM-roofline fraction; "
+                                          "plain_fp32_single is the single-lattice form"}
             line["batched_over_plain"] = round(batched["value"] / plain["value"], 3)
+        if single is not None:
+            line["plain_fp32_single"] = {"value": round(single["value"], 3),
+                                         "ms_per_step": round(single["ms_per_step"], 3),
+                                         "workload": SINGLE_WORKLOAD,
+                                         "roofline": single["roofline"], "gpu_launches": single["launches"]}
+            line["batched_over_plain_single"] = round(batched["value"] / single["value"], 3)
         line.update(bimodal)
         if streaming is not None:
             line["streaming_f16"] = {"value": round(streaming["value"], 3),

@@ -48,3 +48,26 @@ def test_traffic_keys_name_known_kernels():
     # the entries are current: each names the hash of the sources as they stand
     hashes = {bench.kernel_source_hash(), bench.kernel_source_hash(bench.RESIDENT_SOURCES)}
     assert {h for h, _, _ in bench.NCU_TRAFFIC} <= hashes
+
+
+def test_single_lattice_form_gives_every_lattice_its_own_couplings():
+    w = dict(L=4, S=2, n_rep=1, NT=3, Tmin=0.2, Tmax=0.8, n_or=1, measure_every=1)
+    inputs = bench.make_inputs(w, rank=0)
+    samples, J, spins, beta = bench.single_lattice_inputs(inputs)
+    assert samples == list(range(6)) and len(J) == 6 and all(len(s) == 1 for s in spins)
+    # lattice j of sample s keeps its spins and its sample's coupling values
+    assert np.array_equal(spins[4][0], inputs[2][1][1]) and np.array_equal(J[4], inputs[1][1])
+    assert list(beta) == [2.0]
+    ws = bench.WORKLOADS[bench.SINGLE_WORKLOAD]
+    wd = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert ws["S"] == wd["S"] * wd["n_rep"] * wd["NT"] and ws["n_rep"] * ws["NT"] == 1 and ws["L"] == wd["L"]
+    assert ws["prec"] == "f32" and ws["layout"] == "plain"
+
+
+def test_workload_forms():
+    class H:
+        F16, F32, PLAIN, BATCHED = 1, 0, 0, 1
+    assert bench.workload_form(H, bench.WORKLOADS["L8_S1_R2_f32"]) == (H.F32, H.PLAIN)
+    assert bench.workload_form(H, bench.WORKLOADS["L16_S1_R32_f32"]) == (H.F32, H.BATCHED)
+    assert bench.workload_form(H, bench.WORKLOADS[bench.DEFAULT_WORKLOAD]) == (H.F16, H.BATCHED)
+    assert bench.spin_bytes(bench.WORKLOADS["L8_S1_R2_f32"]) == 12 * 2 * 512
