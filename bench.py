@@ -64,9 +64,10 @@ WORKLOADS = {
     "L64_S1_R64_f16": dict(L=64, S=1, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
     # many small lattices of mixed L, every replica set resident in shared
-    # memory (4 replicas x 8 temperatures per sample)
+    # memory (4 replicas x 8 temperatures per sample), both sizes in one
+    # launch per stretch of steps
     "L8x256_L12x256_R32_f16": dict(Ls=(8,) * 256 + (12,) * 256, S=512, n_rep=4, NT=8, Tmin=0.2,
-                                   Tmax=0.8, n_or=8, measure_every=10, persistent=True),
+                                   Tmax=0.8, n_or=8, measure_every=10, persistent=2),
     # mid-size lattices: a replica set (393 KB) is larger than shared memory,
     # so each CTA holds one lattice group for one step and PT runs between
     "L16_S512_R32_f16": dict(L=16, S=512, n_rep=2, NT=16, Tmin=0.15, Tmax=0.75, n_or=8,
@@ -95,9 +96,10 @@ NCU_TRAFFIC = {
     ("f337c22e34aed967", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
     # the L=32 overrelaxation sweep: one launch of 64 samples x 48 lattices
     ("f337c22e34aed967", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
-    # the resident steps of 256 x L=8 + 256 x L=12 samples: both launches of 10 MCS
-    ("a08c3f36068e5e63", "L8x256_L12x256_R32_f16",
-     "k_persistent<2,f16> (10 MCS per launch, one launch per L)"): 361512192,
+    # the resident steps of 256 x L=8 + 256 x L=12 samples, both sizes in one
+    # launch of 10 MCS: 249.1 MB read + 160.8 MB written
+    ("570957506790d731", "L8x256_L12x256_R32_f16",
+     "k_persistent_pair<2,f16> (10 MCS per launch, both lattice sizes in one launch)"): 409880064,
 }
 
 
@@ -342,15 +344,16 @@ def time_or_kernel(lat, torch, n_calls=4, sweeps=8):
     return e0.elapsed_time(e1) / (n_calls * per_sweep * sweeps)
 
 
-def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3):
+def time_persistent_kernel(hsg, w, inputs, torch, n_calls=3, mode=1):
     """Device time of the resident steps for 10 whole MCS without
     measurement, from CUDA events on the library's stream: one launch per
     distinct L plus a counter bump of ~2 us, or, where replica sets span
     several CTAs, per MCS one launch per L, the PT sweep and the bump.
+    With mode 2 both lattice sizes share one launch.
     Returns (ms per 10 MCS, launches per 10 MCS)."""
     samples, J, spins, beta = inputs
     wk = dict(w, measure_every=0)
-    lat = build_lattice(hsg, wk, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=True)
+    lat = build_lattice(hsg, wk, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=mode)
     stream = torch.cuda.current_stream()
     lat.run_steps(MCS_PER_STEP)
     torch.cuda.synchronize()
@@ -411,16 +414,19 @@ def run_form(hsg, torch, dist, wname, inputs, prec, layout, steps, warmup, sampl
     value = updates_rank * dist.world / (ms_max * 1e6)
     if persistent:
         lat.destroy()
-        k_ms, n_kernels = time_persistent_kernel(hsg, w, inputs, torch)
+        k_ms, n_kernels = time_persistent_kernel(hsg, w, inputs, torch, mode=int(persistent))
         upd = R * n_sites * (1 + w["n_or"]) * MCS_PER_STEP
         fpu = flops_per_update(w["n_or"])
         achieved = upd * fpu / (k_ms * 1e-3) / 1e12
         vname = 2 if layout == hsg.BATCHED else 1
         # replica sets that span several CTAs run one MCS per launch, PT between
         split = any(t["groups_per_cta"] * vname < w["NT"] for t in tiling.values())
-        n_res = len(tiling) * (MCS_PER_STEP if split else 1)
-        kname = (f"k_persistent<{vname},f16> (1 MCS per launch, parts of replica sets, PT kernel between)"
-                 if split else f"k_persistent<{vname},f16> ({MCS_PER_STEP} MCS per launch, one launch per L)")
+        one_launch = any(t.get("one_launch") for t in tiling.values())
+        n_res = (1 if one_launch else len(tiling)) * (MCS_PER_STEP if split else 1)
+        kname = (f"k_persistent<{vname},f16> (1 MCS per launch, parts of replica sets, PT kernel between)" if split
+                 else f"k_persistent_pair<{vname},f16> ({MCS_PER_STEP} MCS per launch, both lattice sizes in one launch)"
+                 if one_launch
+                 else f"k_persistent<{vname},f16> ({MCS_PER_STEP} MCS per launch, one launch per L)")
         roof = {"bound": "alu", "kernel": kname,
                 "achieved": round(achieved, 2), "peak": round(ALU_PEAK_TFLOPS, 2),
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
@@ -616,7 +622,9 @@ def workload_config(name, w, world):
                    "no flush: spins per GPU exceed L2 (126 MB)" if spin_bytes(w) > 126e6 else
                    f"no flush: the whole state ({spin_bytes(w) / 1e3:.0f} KB of spins) stays in L2 in any "
                    "run of this size; the workload is latency-bound and not graded against HBM"),
-            "resident": persistent,
+            "resident": bool(persistent),
+            **({"resident_launches": "both lattice sizes in one launch per stretch of steps"}
+               if persistent == 2 else {}),
             "parallelism": f"replicas x{world} (independent samples per GPU)"}
 
 
@@ -689,8 +697,13 @@ def main():
         batched["lat"].destroy()
     streaming = None
     sequential = None
+    joint = None
     if persistent:
         sequential = time_sequential_or(hsg, w, inputs, torch)
+        if persistent == 2:
+            # the same resident steps with one launch per lattice size
+            joint = run_form(hsg, torch, dist, args.workload, inputs, wprec, wlayout, args.steps, args.warmup, None,
+                             peak, persistent=1)
         # the same workload through the streaming kernels, for comparison
         streaming = run_form(hsg, torch, dist, args.workload, inputs, hsg.F16, hsg.BATCHED, args.steps,
                              args.warmup, None, peak)
@@ -720,12 +733,16 @@ def main():
         inputs_s = make_inputs(ws, rank)
         k = max(2, args.steps // 2)
         res = run_form(hsg, torch, dist, SMALL_WORKLOAD, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
-                       persistent=True)
+                       persistent=ws["persistent"])
+        one = run_form(hsg, torch, dist, SMALL_WORKLOAD, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak,
+                       persistent=1)
         strm = run_form(hsg, torch, dist, SMALL_WORKLOAD, inputs_s, hsg.F16, hsg.BATCHED, k, args.warmup, None, peak)
         strm["lat"].destroy()
         small = {"workload": SMALL_WORKLOAD, "steps": k,
                  "resident": {"value": round(res["value"], 3), "ms_per_step": round(res["ms_per_step"], 3),
                               "roofline": res["roofline"], "gpu_launches": res["launches"]},
+                 "resident_per_size": {"value": round(one["value"], 3), "ms_per_step": round(one["ms_per_step"], 3),
+                                       "roofline": one["roofline"], "gpu_launches": one["launches"]},
                  "streaming_f16": {"value": round(strm["value"], 3),
                                    "ms_per_step": round(strm["ms_per_step"], 3)},
                  "resident_over_streaming": round(res["value"] / strm["value"], 3),
@@ -784,6 +801,10 @@ def main():
             line["resident_over_streaming"] = round(batched["value"] / streaming["value"], 3)
         if sequential is not None:
             line["sequential_or_sweep"] = sequential
+        if joint is not None:
+            line["resident_per_size"] = {"value": round(joint["value"], 3),
+                                         "ms_per_step": round(joint["ms_per_step"], 3),
+                                         "roofline": joint["roofline"], "gpu_launches": joint["launches"]}
         if small is not None:
             line["small_lattices"] = small
         if mid is not None:

@@ -117,13 +117,23 @@ typedef struct {
                              shared memory.  Where a replica set (the N_T
                              lattices of one replica of one sample) fits in
                              one CTA, whole steps, PT included, run in one
-                             launch per stretch of steps between measurements;
-                             otherwise each CTA holds part of a set for one
-                             step and the PT sweep follows as its own kernel.
-                             Needs N_T <= 64, N_T a multiple of the layout's
-                             lattices per element, and one lattice group,
-                             12 V L^3 bytes (V = 1 plain, 2 batched), within
-                             224 KiB for every L (HSG_EINVAL otherwise).
+                             launch per lattice size and stretch of steps
+                             between measurements; otherwise each CTA holds
+                             part of a set for one step and the PT sweep
+                             follows as its own kernel.  Needs N_T <= 64, N_T
+                             a multiple of the layout's lattices per element,
+                             and one lattice group, 12 V L^3 bytes (V = 1
+                             plain, 2 batched), within 224 KiB for every L
+                             (HSG_EINVAL otherwise).
+                             2: as 1, with the samples of both lattice sizes
+                             of a two-size context in one launch: CTAs of the
+                             larger size hold one replica set each, CTAs of
+                             the smaller size as many whole sets of one
+                             sample as fit in the same shared memory.  Needs
+                             every replica set held whole (HSG_EINVAL
+                             otherwise); specialised for L = 12 with L = 8 in
+                             the batched layout, generic (bonds read from
+                             global memory) for other pairs.
                              0: streaming steps. */
   double bimodal_D;       /* HSG_BIMODAL: the magnitude D >= 0 of the
                              anisotropic couplings (the paper uses 0.5 and 1);
@@ -266,8 +276,10 @@ hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[5]);
 /* Resident steps (persistent contexts) of `sample`'s lattice size: out[0] =
  * bond residency (0 global, 1 shared as stored, 2 shared as FP32), out[1] =
  * lattice groups per work item, out[2] = threads per CTA, out[3] = lattice
- * groups per CTA (N_T / V: whole replica sets); zeros otherwise. */
-hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]);
+ * groups per CTA (N_T / V per whole replica set), out[4] = whole replica sets
+ * per CTA, out[5] = 1 when all lattice sizes run in one launch; zeros
+ * otherwise. */
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[6]);
 
 /* Autotuner (Sec. III's sweeps; the tiling is free, the results do not
  * depend on it).  For each lattice size of the context it times the

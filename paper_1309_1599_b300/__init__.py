@@ -217,7 +217,7 @@ class Lattice:
         cfg.timeout_cycles = int(timeout_cycles)
         cfg.sweep_kernel = int(sweep_kernel)
         cfg.band_rows = int(band_rows)
-        cfg.persistent = 1 if persistent else 0
+        cfg.persistent = int(persistent)
         cfg.bimodal_D = float(bimodal_D)
         cfg.fused_groups = int(fused_groups)
         self.coupling_prec = int(coupling_prec)
@@ -381,10 +381,10 @@ class Lattice:
                 "groups_per_thread_or": int(out[3]), "groups_per_thread_hb": int(out[4])}
 
     def get_resident_plan(self, sample: int = 0) -> dict:
-        out = np.zeros(4, dtype=np.int32)
+        out = np.zeros(6, dtype=np.int32)
         _check(self._lib.hsg_get_resident_plan(self._h, sample, _ptr(out)))
         return {"bond_residency": int(out[0]), "groups_per_item": int(out[1]), "threads": int(out[2]),
-                "groups_per_cta": int(out[3])}
+                "groups_per_cta": int(out[3]), "sets_per_cta": int(out[4]), "one_launch": bool(out[5])}
 
     def autotune(self) -> None:
         """Time the candidate launch shapes on this context's data and keep

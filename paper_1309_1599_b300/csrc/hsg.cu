@@ -67,6 +67,7 @@ struct Bucket {
   int res_gp = 1;             // resident steps: lattice groups per work item
   int res_threads = 512;      // resident steps: threads per CTA
   int res_gsub = 0;           // resident steps: lattice groups per CTA (N_T/V: whole sets)
+  int res_sets = 1;           // resident steps: whole replica sets per CTA (> 1 only in a joint launch)
 };
 
 }  // namespace
@@ -106,7 +107,13 @@ struct hsg_ctx {
   uint64_t g_step_launches[2][2] = {{0, 0}, {0, 0}};  // kernels per graph replay
   int* d_status = nullptr;     // device status word (HSG_ETIMEOUT from bounded waits)
   bool persistent = false;     // run_steps keeps replica sets resident in shared memory
+  bool persistent_joint = false;  // ... with all lattice sizes in one launch
   bool res_split = false;      // some replica set spans several CTAs: one step per launch, PT outside
+  bool res_pair = false;       // the resident steps of both buckets run in one launch
+  int pair_a = -1, pair_b = -1;  // joint launch: bucket of the first CTAs, bucket of the others
+  bool pair_special = false;   // joint launch: the L = 12 with L = 8 specialisation
+  int pair_threads = 0;        // joint launch: threads per CTA
+  size_t pair_smem = 0;        // joint launch: dynamic shared memory per CTA
   long long timeout_cycles = 0;
   int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
@@ -469,6 +476,32 @@ void* persistent_kernel(int V, int prec, int js, int L, int gp) {
   });
 }
 
+// The joint resident kernel of two buckets: the L = 12 with L = 8
+// specialisation (two lattices per element, L = 12 bonds resident as stored,
+// the L = 8 bucket's bonds as stored (jsb = 1) or as FP32 (jsb = 2), two
+// groups per work item), or the generic one (run-time L, bonds from global
+// memory, one group per item).
+template <int V, int PREC>
+void* pair_fn(bool special, int jsb) {
+  if constexpr (V == 2) {
+    if (special) {
+      if constexpr (PREC == kPrecF32) {
+        return reinterpret_cast<void*>(k_persistent_pair<V, PREC, 1, 12, 2, 1, 8, 2>);
+      } else {
+        return jsb == 2 ? reinterpret_cast<void*>(k_persistent_pair<V, PREC, 1, 12, 2, 2, 8, 2>)
+                        : reinterpret_cast<void*>(k_persistent_pair<V, PREC, 1, 12, 2, 1, 8, 2>);
+      }
+    }
+  }
+  return reinterpret_cast<void*>(k_persistent_pair<V, PREC, 0, 0, 1, 0, 0, 1>);
+}
+
+void* pair_kernel(int V, int prec, bool special, int jsb) {
+  return dispatch(V, prec, [&](auto v, auto pr) {
+    return pair_fn<decltype(v)::value, decltype(pr)::value>(special, jsb);
+  });
+}
+
 // Lattice groups per work item of the resident kernel: two where a
 // specialisation exists and the groups a CTA holds pair up.
 int persistent_gp(int V, int g_sub, int js, int L) {
@@ -549,8 +582,79 @@ hsg_status plan_persistent(hsg_ctx* h) {
     b.res_gsub = best_gsub;
     b.res_gp = persistent_gp(h->V, best_gsub, best_js, b.L);
     b.res_threads = best_threads;
+    b.res_sets = 1;
     if (best_gsub < G_set) h->res_split = true;
   }
+  h->res_pair = false;
+  return HSG_OK;
+}
+
+// Plans the resident steps of a two-bucket context as one launch: bucket a
+// (the larger L) holds one replica set per CTA as planned alone; bucket b
+// holds as many whole replica sets of one sample per CTA (a divisor of
+// n_replicas) as fit in the shared memory bucket a's CTAs take, so the
+// launch's one block shape and shared-memory size serve both.  HSG_EINVAL if
+// a replica set cannot be held whole or the buckets do not fit.
+hsg_status plan_joint(hsg_ctx* h) {
+  if (h->buckets.size() != 2) return HSG_OK;  // one lattice size: one launch already
+  if (h->res_split)
+    return fail(HSG_EINVAL, "one launch for all lattice sizes needs every replica set held whole by a CTA");
+  int dev = 0, optin = 0;
+  HSG_CUDA(cudaGetDevice(&dev));
+  HSG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int ia = h->buckets[0].N >= h->buckets[1].N ? 0 : 1, ib = 1 - ia;
+  Bucket& A = h->buckets[ia];
+  Bucket& B = h->buckets[ib];
+  const bool special = (h->V == 2 && A.L == 12 && B.L == 8);
+  const size_t stored = h->prec == HSG_F16 ? 12 : h->prec == HSG_BIMODAL ? 1 : 24;
+  const size_t bond_bytes[3] = {0, stored, 24};
+  const int G_set = h->NT / h->V;
+  const int jsa = special ? 1 : 0;
+  const size_t smem_a = static_cast<size_t>(12) * h->V * G_set * A.N + 3 * static_cast<size_t>(A.N) * bond_bytes[jsa];
+  std::vector<int> jsbs;
+  if (special && h->prec != HSG_F32) jsbs.push_back(2);
+  jsbs.push_back(special ? 1 : 0);
+  int best_k = 0, best_jsb = 0;
+  size_t best_smem = 0;
+  for (int k = h->n_rep; k >= 1 && best_k == 0; --k) {
+    if (h->n_rep % k != 0 || k * h->NT > kMaxTempsResident) continue;
+    for (const int jsb : jsbs) {
+      const size_t smem_b =
+          static_cast<size_t>(12) * h->V * k * G_set * B.N + 3 * static_cast<size_t>(B.N) * bond_bytes[jsb];
+      if (smem_b > smem_a) continue;  // bucket a's CTAs set the launch's shared memory
+      best_k = k;
+      best_jsb = jsb;
+      best_smem = smem_a;
+      break;
+    }
+  }
+  if (best_k == 0) return fail(HSG_EINVAL, "no joint resident plan for these lattice sizes");
+  void* fn = pair_kernel(h->V, h->prec, special, best_jsb);
+  cudaFuncAttributes fa;
+  HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
+  if (best_smem + fa.sharedSizeBytes > static_cast<size_t>(optin))
+    return fail(HSG_EINVAL, "a replica set of L = " + std::to_string(A.L) + " does not fit one CTA of the joint launch");
+  HSG_TRY(raise_smem_limit(fn, static_cast<size_t>(optin) - fa.sharedSizeBytes));
+  const int threads = std::min(fa.maxThreadsPerBlock, std::max(A.res_threads, B.res_threads)) / 32 * 32;
+  int occ = 0;
+  HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, best_smem));
+  if (occ < 1) return fail(HSG_EINVAL, "the joint resident launch does not fit an SM");
+  A.res_js = jsa;
+  A.res_gp = special ? 2 : 1;
+  A.res_gsub = G_set;
+  A.res_sets = 1;
+  B.res_js = best_jsb;
+  B.res_gp = special ? 2 : 1;
+  B.res_gsub = best_k * G_set;
+  B.res_sets = best_k;
+  A.res_smem = B.res_smem = best_smem;
+  A.res_threads = B.res_threads = threads;
+  h->res_pair = true;
+  h->pair_a = ia;
+  h->pair_b = ib;
+  h->pair_special = special;
+  h->pair_threads = threads;
+  h->pair_smem = best_smem;
   return HSG_OK;
 }
 
@@ -580,6 +684,7 @@ PersistentParams persistent_params(hsg_ctx* h, const Bucket& b, int steps) {
   p.counters = h->d_counters;
   p.D = h->bimodal_D;
   p.G_sub = b.res_gsub;
+  p.sets = b.res_sets;
   p.pt = h->res_split ? 0 : 1;
   return p;
 }
@@ -594,6 +699,20 @@ hsg_status launch_persistent(hsg_ctx* h, const Bucket& b, PersistentParams p, in
   return HSG_OK;
 }
 
+// The joint launch: bucket pair_a's CTAs (one replica set each) first, then
+// bucket pair_b's (res_sets whole sets of one sample each).
+hsg_status launch_pair(hsg_ctx* h, PersistentParams pa, PersistentParams pb, int threads, cudaStream_t st) {
+  const Bucket& A = h->buckets[h->pair_a];
+  const Bucket& B = h->buckets[h->pair_b];
+  int ctas_a = A.S_b * h->n_rep;
+  const int ctas_b = B.S_b * (h->n_rep / B.res_sets);
+  void* args[] = {&pa, &pb, &ctas_a};
+  *h->launch_sink += 1;
+  HSG_CUDA(cudaLaunchKernel(pair_kernel(h->V, h->prec, h->pair_special, B.res_js), dim3(ctas_a + ctas_b),
+                            dim3(threads), args, h->pair_smem, st));
+  return HSG_OK;
+}
+
 hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st);
 
 // `steps` whole Monte Carlo steps with the lattices resident in shared
@@ -602,8 +721,13 @@ hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st);
 // counters advance.
 hsg_status enqueue_persistent(hsg_ctx* h, int steps, cudaStream_t st) {
   if (h->res_split && steps != 1) return fail(HSG_ESTATE, "split replica sets run one step per launch");
-  for (const Bucket& b : h->buckets)
-    HSG_TRY(launch_persistent(h, b, persistent_params(h, b, steps), b.res_gp, b.res_threads, st));
+  if (h->res_pair) {
+    HSG_TRY(launch_pair(h, persistent_params(h, h->buckets[h->pair_a], steps),
+                        persistent_params(h, h->buckets[h->pair_b], steps), h->pair_threads, st));
+  } else {
+    for (const Bucket& b : h->buckets)
+      HSG_TRY(launch_persistent(h, b, persistent_params(h, b, steps), b.res_gp, b.res_threads, st));
+  }
   if (h->res_split) HSG_TRY(enqueue_pt(h, st));
   return enqueue_bump(h, static_cast<uint32_t>(steps), static_cast<uint32_t>(steps), st);
 }
@@ -801,7 +925,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
     return fail(HSG_EINVAL, "sweep_kernel must be HSG_SWEEP_AUTO or HSG_SWEEP_TWO_PASS");
   if (cfg->band_rows < 0 || (cfg->band_rows > 0 && cfg->sweep_kernel != HSG_SWEEP_AUTO))
     return fail(HSG_EINVAL, "band_rows must be 0, or > 0 with the fused sweep");
-  if (cfg->persistent != 0 && cfg->persistent != 1) return fail(HSG_EINVAL, "persistent must be 0 or 1");
+  if (cfg->persistent < 0 || cfg->persistent > 2) return fail(HSG_EINVAL, "persistent must be 0, 1 or 2");
   if (cfg->persistent) {
     if (cfg->n_temps > kMaxTempsResident) return fail(HSG_EINVAL, "persistent steps need n_temps <= 64");
     if (cfg->layout == HSG_LAYOUT_BATCHED && cfg->n_temps % 2 != 0)
@@ -850,6 +974,7 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
   h->timeout_cycles = cfg->timeout_cycles > 0 ? cfg->timeout_cycles : 4000000000LL;
   h->sweep_kernel = cfg->sweep_kernel;
   h->persistent = cfg->persistent != 0;
+  h->persistent_joint = cfg->persistent == 2;
   h->launch_sink = &h->launches;
   h->Ls.assign(cfg->L, cfg->L + cfg->n_samples);
   h->beta.assign(cfg->beta, cfg->beta + cfg->n_temps);
@@ -954,7 +1079,8 @@ hsg_status hsg_lattice_create(const hsg_config* cfg, hsg_t* out) {
 
   if (max_fused_smem > 0 && allow_fused_smem_all(V, h->prec, max_fused_smem) != HSG_OK) return bail(HSG_ECUDA);
   if (h->persistent) {
-    const hsg_status ps = plan_persistent(h);
+    hsg_status ps = plan_persistent(h);
+    if (ps == HSG_OK && h->persistent_joint) ps = plan_joint(h);
     if (ps != HSG_OK) return bail(ps);
   }
   {
@@ -1472,7 +1598,7 @@ hsg_status hsg_get_sweep_plan(hsg_t h, int sample, int out[5]) {
   return HSG_OK;
 }
 
-hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]) {
+hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[6]) {
   if (!h || !out) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   const Bucket& b = h->buckets[h->sample_bucket[sample]];
@@ -1480,6 +1606,8 @@ hsg_status hsg_get_resident_plan(hsg_t h, int sample, int out[4]) {
   out[1] = h->persistent ? b.res_gp : 0;
   out[2] = h->persistent ? b.res_threads : 0;
   out[3] = h->persistent ? b.res_gsub : 0;
+  out[4] = h->persistent ? b.res_sets : 0;
+  out[5] = h->res_pair ? 1 : 0;
   return HSG_OK;
 }
 
@@ -1702,6 +1830,78 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
   return st;
 }
 
+// The joint resident launch: threads per CTA, timed on scratch copies of
+// both buckets' spins, labels, energies and acceptances.
+hsg_status tune_pair(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1) {
+  Bucket& A = h->buckets[h->pair_a];
+  Bucket& B = h->buckets[h->pair_b];
+  const std::array<int, 6> key = {2, A.L * 1024 + B.L, h->V, h->prec, h->NT * 256 + B.res_sets, B.res_js};
+  std::array<int, 3> got;
+  if (tune_lookup(key, &got)) {
+    h->pair_threads = A.res_threads = B.res_threads = got[1];
+    return HSG_OK;
+  }
+  void* fn = pair_kernel(h->V, h->prec, h->pair_special, B.res_js);
+  cudaFuncAttributes fa;
+  HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
+  const size_t S = h->S;
+  const size_t na = static_cast<size_t>(A.S_b) * h->R * 3 * A.N, nb = static_cast<size_t>(B.S_b) * h->R * 3 * B.N;
+  float *spa = nullptr, *spb = nullptr;
+  int *perm = nullptr, *temp_of = nullptr;
+  double* E = nullptr;
+  long long* acc = nullptr;
+  hsg_status st = dalloc(&spa, na);
+  if (st == HSG_OK) st = dalloc(&spb, nb);
+  if (st == HSG_OK) st = dalloc(&perm, S * h->n_rep * h->NT);
+  if (st == HSG_OK) st = dalloc(&temp_of, S * h->R);
+  if (st == HSG_OK) st = dalloc(&E, S * h->R);
+  if (st == HSG_OK) st = dalloc(&acc, S * h->n_rep * acc_stride(h));
+  auto run = [&]() -> hsg_status {
+    HSG_CUDA(cudaMemcpyAsync(spa, A.d_spins[A.cur], na * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    HSG_CUDA(cudaMemcpyAsync(spb, B.d_spins[B.cur], nb * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    HSG_CUDA(cudaMemcpyAsync(perm, h->d_perm, S * h->n_rep * h->NT * sizeof(int), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    const int steps = (h->measure_every > 0 && h->measure_every <= kMaxStepsPerLaunch) ? h->measure_every : 10;
+    PersistentParams pa = persistent_params(h, A, steps), pb = persistent_params(h, B, steps);
+    for (PersistentParams* p : {&pa, &pb}) {
+      p->perm = perm;
+      p->temp_of = temp_of;
+      p->E = E;
+      p->accepted = acc;
+    }
+    pa.spins = spa;
+    pb.spins = spb;
+    float best_ms = -1.0f;
+    int best = h->pair_threads;
+    std::vector<int> cands = {h->pair_threads};  // the current plan first
+    for (const int W : {16, 18, 20}) if (32 * W != h->pair_threads) cands.push_back(32 * W);
+    for (const int t : cands) {
+      if (t > fa.maxThreadsPerBlock) continue;
+      int occ = 0;
+      HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, h->pair_smem));
+      if (occ < 1) continue;
+      float ms = 0.0f;
+      HSG_TRY(time_ms(h, e0, e1, 2, [&]() { return launch_pair(h, pa, pb, t, h->stream); }, &ms));
+      if (best_ms < 0.0f || ms < 0.98f * best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    h->pair_threads = A.res_threads = B.res_threads = best;
+    tune_store(key, {0, best, 0});
+    return HSG_OK;
+  };
+  if (st == HSG_OK) st = run();
+  cudaStreamSynchronize(h->stream);
+  cudaFree(spa);
+  cudaFree(spb);
+  cudaFree(perm);
+  cudaFree(temp_of);
+  cudaFree(E);
+  cudaFree(acc);
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1723,8 +1923,9 @@ hsg_status hsg_autotune(hsg_t h) {
   hsg_status st = HSG_OK;
   for (Bucket& b : h->buckets) {
     if (st == HSG_OK && b.fused) st = tune_fused(h, b, e0, e1);
-    if (st == HSG_OK && h->persistent) st = tune_persistent(h, b, e0, e1);
+    if (st == HSG_OK && h->persistent && !h->res_pair) st = tune_persistent(h, b, e0, e1);
   }
+  if (st == HSG_OK && h->res_pair) st = tune_pair(h, e0, e1);
   h->launch_sink = sink;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

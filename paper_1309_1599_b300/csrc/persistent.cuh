@@ -59,6 +59,8 @@ constexpr int persistent_max_threads() {
 template <int LT>
 constexpr int persistent_min_blocks() { return (LT == 8 || LT == 16) ? 2 : 1; }
 constexpr int kMaxTempsResident = 64;
+// Block limit of the two-bucket launch: the larger of its buckets' limits.
+constexpr int kPairMaxThreads = 640;
 constexpr int kMaxStepsPerLaunch = 256;
 
 struct PersistentParams {
@@ -75,10 +77,23 @@ struct PersistentParams {
   uint2 key;
   const uint32_t* counters;  // [0] heat-bath sweeps, [1] PT sweeps (at launch)
   float D;                 // bimodal couplings: magnitude of the anisotropy
-  int G_sub;               // lattice groups per CTA: N_T/V (a whole replica set)
-                           // or a divisor of it
-  int pt;                  // 1: PT in the kernel (G_sub = N_T/V); 0: one step per
+  int G_sub;               // lattice groups per CTA: sets * N_T/V (whole replica
+                           // sets) or a divisor of N_T/V (part of one set)
+  int sets;                // whole replica sets per CTA (a divisor of n_rep, with
+                           // sets * N_T <= kMaxTempsResident), 1 for parts of a set
+  int pt;                  // 1: PT in the kernel (whole sets); 0: one step per
                            // launch, energies out, the PT sweep by the caller
+};
+
+// The CTA-wide tables of a resident CTA, indexed by local lattice (the
+// lattices a CTA holds, numbered from its first slot) or, for the labels and
+// acceptances, by set * N_T + temperature.
+struct PersistentShared {
+  double* E;          // [kMaxTempsResident] energy of each local lattice
+  double* part;       // [2 kMaxTempsResident] per (group, warp of the group, lattice)
+  float* beta_lat;    // [kMaxTempsResident] beta of each local lattice
+  int* perm;          // [kMaxTempsResident] (set, temperature) -> local lattice
+  int* acc;           // [kMaxTempsResident] accepted swaps per (set, pair)
 };
 
 
@@ -358,37 +373,47 @@ __device__ __forceinline__ int colour_split_index(int i, int L, int N) {
   return c * (N >> 1) + row * half + k;
 }
 
-// K whole steps of every replica set of one L.  V: lattices per element;
-// PREC: stored coupling precision; JS: bond residency (see above); LT: L as
-// a compile-time constant, or 0 for the runtime p.L; GP: lattice groups per
-// work item (2: each bond read and converted once for two groups).
-template <int V, int PREC, int JS, int LT, int GP = 1>
-__global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_blocks<LT>())
-    k_persistent(PersistentParams p) {
-  extern __shared__ __align__(16) float sp[];
-  __shared__ double s_E[kMaxTempsResident];
-  __shared__ double s_part[kMaxTempsResident * 2];  // per (group, warp of the group, lattice)
-  __shared__ float s_beta_lat[kMaxTempsResident];   // beta of each local lattice
-  __shared__ int s_perm[kMaxTempsResident];         // temperature -> local lattice
-  __shared__ int s_acc[kMaxTempsResident];
-
+// K whole steps of the replica sets one CTA holds, for one L: the body of
+// the resident kernels.  cta: the CTA's index among those of its bucket.
+// V: lattices per element; PREC: stored coupling precision; JS: bond
+// residency (see above); LT: L as a compile-time constant, or 0 for the
+// runtime p.L; GP: lattice groups per work item (2: each bond read and
+// converted once for two groups).
+template <int V, int PREC, int JS, int LT, int GP>
+__device__ __forceinline__ void persistent_body(const PersistentParams& p, const int cta, float* sp,
+                                                const PersistentShared& sh) {
+  double* s_E = sh.E;
+  double* s_part = sh.part;
+  float* s_beta_lat = sh.beta_lat;
+  int* s_perm = sh.perm;
+  int* s_acc = sh.acc;
   const int NT = p.NT;
+  const int sets = p.sets;                                // whole replica sets held (1: a set or part of one)
   const int G_sub = p.G_sub;                              // groups held by this CTA
-  const int n_sub = NT / V / G_sub;                       // CTAs per replica set
-  const bool whole = p.pt != 0;                           // whole replica set, PT here
+  const bool whole = p.pt != 0;                           // whole replica sets, PT here
   const int NT_loc = G_sub * V;                           // lattices held by this CTA
-  const int sr = blockIdx.x / n_sub, part = blockIdx.x - sr * n_sub;
-  const int sb = sr / p.n_rep, r = sr - sb * p.n_rep;
+  int sb, r0, part;
+  if (sets > 1) {                                         // several whole sets of one sample
+    const int cps = p.n_rep / sets;
+    sb = cta / cps;
+    r0 = (cta - sb * cps) * sets;
+    part = 0;
+  } else {                                                // one set, or part n of one
+    const int n_sub = NT / V / G_sub;                     // CTAs per replica set
+    const int sr = cta / n_sub;
+    part = cta - sr * n_sub;
+    sb = sr / p.n_rep;
+    r0 = sr - sb * p.n_rep;
+  }
   const int sg = p.sample_ids[sb];
   const int L = LT > 0 ? LT : p.L;
   const int N = L * L * L;
-  float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r) * (NT / V) +
+  float* gsp = p.spins + (static_cast<size_t>(sb) * p.G + static_cast<size_t>(r0) * (NT / V) +
                           static_cast<size_t>(part) * G_sub) * 3 * N * V;
   const void* Jg = sample_bonds<PREC>(p.J, sb, N);
   void* Js = sp + static_cast<size_t>(NT_loc) * 3 * N;    // after the spins (16-byte aligned)
-  const int loc0 = r * NT + part * NT_loc;                // first local lattice's slot
+  const int loc0 = r0 * NT + part * NT_loc;               // first local lattice's slot
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(loc0);
-  const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + r;
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
   const int G_set = G_sub;                                // groups swept by this CTA
   const ResidentWarps rw = resident_warps(G_set / GP);
@@ -432,13 +457,14 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
       }
     }
   }
-  if (threadIdx.x < NT) {
-    const int k = threadIdx.x;
-    const int slot = p.perm[(static_cast<size_t>(sg) * p.n_rep + r) * NT + k];
-    s_perm[k] = slot - r * NT;
+  // labels of the sets held: (set j, temperature k) -> local lattice
+  for (int q = threadIdx.x; q < sets * NT; q += blockDim.x) {
+    const int j = q / NT, k = q - j * NT;
+    const int slot = p.perm[(static_cast<size_t>(sg) * p.n_rep + r0 + j) * NT + k];
     const int li = slot - loc0;
+    s_perm[q] = li;
     if (li >= 0 && li < NT_loc) s_beta_lat[li] = static_cast<float>(p.beta[k]);
-    s_acc[k] = 0;
+    s_acc[q] = 0;
   }
   __syncthreads();
 
@@ -477,22 +503,26 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
       s_E[threadIdx.x] = e;
     }
     __syncthreads();
-    // parallel tempering within the replica set (App. A.1), when this CTA
-    // holds all of it
-    if (whole && threadIdx.x == 0 && NT > 1) {
+    // parallel tempering within each replica set (App. A.1) this CTA holds
+    // whole, one thread per set
+    if (whole && threadIdx.x < sets && NT > 1) {
+      const int j = threadIdx.x;
+      const uint32_t gset = static_cast<uint32_t>(sg) * p.n_rep + static_cast<uint32_t>(r0 + j);
+      int* pm = s_perm + j * NT;
+      int* ac = s_acc + j * NT;
       const uint32_t tp = t_pt0 + static_cast<uint32_t>(step);
       for (int k = 0; k + 1 < NT; ++k) {
         const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(k), gset, tp, kTagTempering), p.key);
         const double u = uniform52(w.x, w.y);
-        const int a = s_perm[k], b = s_perm[k + 1];
+        const int a = pm[k], b = pm[k + 1];
         const double delta = (p.beta[k] - p.beta[k + 1]) * (s_E[a] - s_E[b]);
         if (delta >= 0.0 || u < exp(delta)) {
-          s_perm[k] = b;
-          s_perm[k + 1] = a;
-          s_acc[k] += 1;
+          pm[k] = b;
+          pm[k + 1] = a;
+          ac[k] += 1;
         }
       }
-      for (int k = 0; k < NT; ++k) s_beta_lat[s_perm[k]] = static_cast<float>(p.beta[k]);
+      for (int k = 0; k < NT; ++k) s_beta_lat[pm[k]] = static_cast<float>(p.beta[k]);
     }
     __syncthreads();
   }
@@ -506,19 +536,51 @@ __global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_b
       dst[q] = src[gc * N + colour_split_index(i, L, N)];
     }
   }
-  if (!whole) {  // part of a replica set: its energies only; PT follows
-    if (threadIdx.x < NT_loc) p.E[static_cast<size_t>(sg) * p.R + loc0 + threadIdx.x] = s_E[threadIdx.x];
-  } else if (threadIdx.x < NT) {
-    const int k = threadIdx.x;
-    const size_t pbase = (static_cast<size_t>(sg) * p.n_rep + r) * NT;
-    p.perm[pbase + k] = s_perm[k] + r * NT;
-    p.temp_of[static_cast<size_t>(sg) * p.R + r * NT + s_perm[k]] = k;
-    p.E[static_cast<size_t>(sg) * p.R + r * NT + k] = s_E[k];
-    if (k + 1 < NT || NT == 1) {
-      const int stride = NT > 1 ? NT - 1 : 1;
-      p.accepted[(static_cast<size_t>(sg) * p.n_rep + r) * stride + k] += s_acc[k];
+  if (threadIdx.x < NT_loc) p.E[static_cast<size_t>(sg) * p.R + loc0 + threadIdx.x] = s_E[threadIdx.x];
+  if (whole) {  // labels and acceptances of the sets held (parts of a set: PT follows)
+    for (int q = threadIdx.x; q < sets * NT; q += blockDim.x) {
+      const int j = q / NT, k = q - j * NT;
+      const size_t pbase = (static_cast<size_t>(sg) * p.n_rep + r0 + j) * NT;
+      const int li = s_perm[q];
+      p.perm[pbase + k] = li + loc0;
+      p.temp_of[static_cast<size_t>(sg) * p.R + loc0 + li] = k;
+      if (k + 1 < NT || NT == 1) {
+        const int stride = NT > 1 ? NT - 1 : 1;
+        p.accepted[(static_cast<size_t>(sg) * p.n_rep + r0 + j) * stride + k] += s_acc[q];
+      }
     }
   }
+}
+
+#define HSG_PERSISTENT_SHARED                                                    \
+  extern __shared__ __align__(16) float sp[];                                     \
+  __shared__ double s_E[kMaxTempsResident];                                       \
+  __shared__ double s_part[kMaxTempsResident * 2];                                \
+  __shared__ float s_beta_lat[kMaxTempsResident];                                 \
+  __shared__ int s_perm[kMaxTempsResident];                                       \
+  __shared__ int s_acc[kMaxTempsResident];                                        \
+  const PersistentShared sh{s_E, s_part, s_beta_lat, s_perm, s_acc}
+
+// Resident steps of one bucket (one L): CTA b holds the sets numbered b.
+template <int V, int PREC, int JS, int LT, int GP = 1>
+__global__ void __launch_bounds__(persistent_max_threads<LT>(), persistent_min_blocks<LT>())
+    k_persistent(PersistentParams p) {
+  HSG_PERSISTENT_SHARED;
+  persistent_body<V, PREC, JS, LT, GP>(p, blockIdx.x, sp, sh);
+}
+
+// Resident steps of two buckets of different L in one launch: the first
+// ctas_a CTAs run bucket a, the others bucket b, all with the launch's block
+// size and shared memory (the larger of the two buckets' needs), so the
+// CTAs of both sizes share the GPU and neither bucket's last wave runs alone.
+template <int V, int PREC, int JSA, int LA, int GPA, int JSB, int LB, int GPB>
+__global__ void __launch_bounds__(kPairMaxThreads, 1)
+    k_persistent_pair(PersistentParams a, PersistentParams b, int ctas_a) {
+  HSG_PERSISTENT_SHARED;
+  if (static_cast<int>(blockIdx.x) < ctas_a)
+    persistent_body<V, PREC, JSA, LA, GPA>(a, blockIdx.x, sp, sh);
+  else
+    persistent_body<V, PREC, JSB, LB, GPB>(b, blockIdx.x - ctas_a, sp, sh);
 }
 
 }  // namespace hsg

@@ -60,6 +60,64 @@ def test_persistent_steps_equal_streaming_steps(case):
     assert b.get_launch_count() < a.get_launch_count()
 
 
+JOINT = [
+    # Ls, n_temps, n_rep, prec, layout, steps: the L = 12 with L = 8
+    # specialisation (L = 8 CTAs holding 4, 2 sets; FP16 and FP32 bonds) and
+    # the generic joint kernel (other sizes, bonds from global memory)
+    ([12, 8, 8, 12], 8, 4, hsg.F16, hsg.BATCHED, 5),
+    ([8, 12], 8, 2, hsg.F16, hsg.BATCHED, 4),
+    ([8, 12], 4, 2, hsg.F32, hsg.BATCHED, 4),
+    ([6, 10, 6], 4, 2, hsg.F16, hsg.PLAIN, 4),
+    ([10, 4], 6, 3, hsg.F32, hsg.BATCHED, 4),
+]
+
+
+@pytest.mark.parametrize("case", JOINT, ids=lambda c: f"L{'-'.join(map(str, c[0]))}_T{c[1]}_R{c[2]}")
+def test_joint_launch_of_two_lattice_sizes_equals_streaming(case):
+    """persistent = 2: the resident steps of both lattice sizes in one launch
+    per stretch of steps (CTAs of the smaller size holding several whole
+    replica sets of one sample) give the streaming path's spins bit for bit,
+    the same labels, acceptances and counters, and energies and observables
+    equal up to the summation order of the energies; one resident launch per
+    stretch instead of one per lattice size."""
+    Ls, NT, n_rep, prec, layout, steps = case
+    betas = gi.linear_betas(0.2, 1.2, NT)
+    a, _ = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout, n_or=2, measure_every=2)
+    b, _ = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout, n_or=2, measure_every=2, persistent=2)
+    c, _ = make(Ls, betas, n_rep=n_rep, prec=prec, layout=layout, n_or=2, measure_every=2, persistent=1)
+    small = Ls.index(min(Ls))
+    plan = b.get_resident_plan(small)
+    assert plan["one_launch"] and plan["sets_per_cta"] >= 1
+    assert not c.get_resident_plan(small)["one_launch"]
+    n = []
+    for lat in (a, b, c):
+        l0 = lat.get_launch_count()
+        lat.run_steps(steps)
+        n.append(lat.get_launch_count() - l0)
+    stretches = (steps + 1) // 2
+    assert n[1] == n[2] - stretches, n           # one resident launch instead of two per stretch
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.get_perm(), b.get_perm())
+    assert np.array_equal(a.get_pt_accepts(), b.get_pt_accepts())
+    assert np.array_equal(a.get_counters(), b.get_counters())
+    Ea, Eb = a.get_energies(), b.get_energies()
+    assert np.allclose(Ea, Eb, rtol=1e-9, atol=1e-9 * np.abs(Ea).max()), np.abs(Ea - Eb).max()
+    oa, ca = a.read_observables()
+    ob, cb = b.read_observables()
+    assert np.array_equal(ca, cb)
+    assert np.allclose(oa, ob, rtol=1e-9, atol=1e-12)
+    for lat in (a, b, c):
+        lat.destroy()
+
+
+def test_joint_launch_refused_when_sets_cannot_be_held_whole():
+    """persistent = 2 needs every replica set held whole by one CTA: L = 16
+    with 8 temperatures splits its sets (393 KB), so the context is refused."""
+    with pytest.raises(hsg.HsgError, match="whole"):
+        hsg.Lattice([16, 8], gi.linear_betas(0.2, 1.2, 8), n_replicas=2, coupling_prec=hsg.F16,
+                    layout=hsg.BATCHED, persistent=2)
+
+
 def test_persistent_step_matches_oracle_step_from_equilibrium():
     """One whole step (HB + 8 OR + energies + PT) of the resident kernel from
     an equilibrated state (overrelaxation amplifies rounding differences less
@@ -86,8 +144,9 @@ def test_persistent_step_matches_oracle_step_from_equilibrium():
         assert abs(E[j] - ref) <= 2e-6 * abs(ref)
 
 
-@pytest.mark.parametrize("name", ["L8x256_L12x256_R32_f16", "L16_S512_R32_f16"])
-def test_bench_resident_workloads_equal_streaming(name):
+@pytest.mark.parametrize("name,mode", [("L8x256_L12x256_R32_f16", 1), ("L8x256_L12x256_R32_f16", 2),
+                                       ("L16_S512_R32_f16", 1)])
+def test_bench_resident_workloads_equal_streaming(name, mode):
     """The resident workloads at the size and launch configuration bench.py
     times, with shapes chosen by the autotuner: the mixed small lattices (256
     samples of L=8 and 256 of L=12, 4 replicas x 8 temperatures; whole
@@ -97,23 +156,28 @@ def test_bench_resident_workloads_equal_streaming(name):
     One bench step of 10 MCS with resident launches equals the streaming
     kernels on every lattice bit for bit, with the same labels, acceptances
     and counters, and energies and observables equal up to their summation
-    order."""
+    order.  Mode 2 runs both lattice sizes of the mixed workload in one
+    resident launch per step (one launch fewer than mode 1)."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     w = bench.WORKLOADS[name]
     samples, J, spins, beta = bench.make_inputs(w, 0)
+    modes = (False, mode, 1) if mode == 2 else (False, mode)
     lats = [bench.build_lattice(hsg, w, samples, J, spins, beta, hsg.F16, hsg.BATCHED, persistent=p)
-            for p in (False, True)]
+            for p in modes]
     del spins
     launches = []
     for lat in lats:
         l0 = lat.get_launch_count()
         lat.run_steps(bench.MCS_PER_STEP)
         launches.append(lat.get_launch_count() - l0)
-    a, b = lats
+    a, b = lats[0], lats[1]
     assert launches[1] < launches[0], launches
+    if mode == 2:
+        assert launches[1] == launches[2] - 1, launches
+        assert b.get_resident_plan(0)["one_launch"]
     for s in range(a.S):
         assert np.array_equal(a.get_spins_sample(s), b.get_spins_sample(s)), s
     assert np.array_equal(a.get_perm(), b.get_perm())
