@@ -1,12 +1,15 @@
-"""Writes tests/golden/pt_L16_oracle.json: block averages of independent
-FP64 oracle chains on the parallel-tempering workload (L=16, the couplings
-of disorder sample 0, 16 temperatures evenly spaced in [0.15, 0.75] x 2
-replicas, 20000 steps of one heat-bath + 8 overrelaxation sweeps + one PT
-sweep, observables every 10 steps).  Chain c starts from the random spins of
-generator sample c and uses the random streams of sample index c, as chain c
-of the GPU test does.  Calls only the oracle and the seeded input generator.
+"""Writes tests/golden/pt_L16_oracle.json (FP32-stored couplings) or, with
+--f16, tests/golden/pt_L16_f16_oracle.json (the same Gaussian draws rounded
+once to FP16, the values the FP16-coupling GPU form stores): block averages
+of independent FP64 oracle chains on the parallel-tempering workload (L=16,
+the couplings of disorder sample 0, 16 temperatures evenly spaced in
+[0.15, 0.75] x 2 replicas, 20000 steps of one heat-bath + 8 overrelaxation
+sweeps + one PT sweep, observables every 10 steps).  Chain c starts from the
+random spins of generator sample c and uses the random streams of sample
+index c, as chain c of the GPU test does.  Calls only the oracle and the
+seeded input generator.
 
-    python tests/golden/make_pt_L16_oracle.py      # 8 chains in parallel
+    python tests/golden/make_pt_L16_oracle.py [--f16]     # 8 chains in parallel
 """
 import json
 import multiprocessing as mp
@@ -21,13 +24,14 @@ L, N_T, N_REP, SEED, N_CHAINS = 16, 16, 2, 1, 8
 STEPS, BLOCK, MEASURE_EVERY, N_OR = 20000, 1000, 10, 8
 
 
-def chain(c):
+def chain(args):
+    c, precision = args
     import numpy as np
 
     import hsg_inputs as gi
     import oracle
     beta = gi.linear_betas(0.15, 0.75, N_T)
-    J6 = gi.couplings(L, SEED, 0)
+    J6 = gi.couplings(L, SEED, 0, precision=precision)
     spins = gi.random_spins_batch(L, SEED, c, N_T * N_REP)
     smp = oracle.Sample(L, J6, spins, beta, N_REP, SEED, sample_index=c)
     blocks = []
@@ -48,15 +52,17 @@ def chain(c):
 
 
 def main():
+    precision = "f16" if "--f16" in sys.argv else "f32"
     ctx = mp.get_context("spawn")
     with ctx.Pool(N_CHAINS) as pool:
-        res = pool.map(chain, range(N_CHAINS))
+        res = pool.map(chain, [(c, precision) for c in range(N_CHAINS)])
     import oracle
     out = {"L": L, "n_temps": N_T, "n_replicas": N_REP, "seed": SEED, "steps": STEPS,
            "block_steps": BLOCK, "measure_every": MEASURE_EVERY, "n_or": N_OR,
-           "T_range": [0.15, 0.75], "observables": list(oracle.OBS_NAMES),
+           "T_range": [0.15, 0.75], "couplings": precision, "observables": list(oracle.OBS_NAMES),
            "chains": [r[0] for r in res], "pt_accepted": [r[1] for r in res]}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pt_L16_oracle.json")
+    name = "pt_L16_f16_oracle.json" if precision == "f16" else "pt_L16_oracle.json"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
         json.dump(out, f)
     print("wrote", path)

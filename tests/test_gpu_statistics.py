@@ -48,12 +48,14 @@ def _t_stat(a, b):
     return (a.mean(0) - b.mean(0)) / np.sqrt(sp2 * (1.0 / na + 1.0 / nb) + 1e-300)
 
 
-def _gpu_chains(L, beta, n_rep, n_chains, steps, measure_every, layout, seed=1):
-    """n_chains independent chains on the couplings of generator sample 0:
-    chain c = context sample c (its own initial spins and random streams)."""
-    lat = hsg.Lattice([L] * n_chains, beta, n_replicas=n_rep, coupling_prec=hsg.F32,
+def _gpu_chains(L, beta, n_rep, n_chains, steps, measure_every, layout, seed=1, precision="f32"):
+    """n_chains independent chains on the couplings of generator sample 0
+    (stored as FP32, or rounded once to FP16 with precision="f16"): chain c =
+    context sample c (its own initial spins and random streams)."""
+    prec = hsg.F16 if precision == "f16" else hsg.F32
+    lat = hsg.Lattice([L] * n_chains, beta, n_replicas=n_rep, coupling_prec=prec,
                       layout=layout, n_or=8, measure_every=measure_every, seed=seed)
-    J6 = gi.couplings(L, seed, 0)
+    J6 = gi.couplings(L, seed, 0, precision=precision)
     for c in range(n_chains):
         lat.set_couplings(c, J6)
         for j in range(lat.R):
@@ -86,19 +88,23 @@ def test_long_run_L8_single_temperature_matches_oracle():
     assert np.asarray(gpu)[:, 0].std() > 0
 
 
-def test_parallel_tempering_L16_matches_stored_oracle():
+@pytest.mark.parametrize("golden", ["pt_L16_oracle.json", "pt_L16_f16_oracle.json"])
+def test_parallel_tempering_L16_matches_stored_oracle(golden):
     """L=16, the couplings of sample 0, 16 temperatures evenly spaced in
     [0.15, 0.75] x 2 replicas, 20000 steps of HB + 8 OR + PT, observables
     every 10 steps.  Averages over the second half of 16 GPU chains against
     the 8 oracle chains stored by tests/golden/make_pt_L16_oracle.py, for
     e, q2, q2(k_min) and q2_CG at every temperature (64 statistics): all
-    |t| < 4 and mean t^2 < 2; the energies |t| < 3."""
-    with open(os.path.join(HERE, "golden", "pt_L16_oracle.json")) as f:
+    |t| < 4 and mean t^2 < 2; the energies |t| < 3.  Once with the couplings
+    stored as FP32 and once with the same draws rounded to FP16 (the
+    precision form: the oracle runs in FP64 on the identical FP16 values)."""
+    with open(os.path.join(HERE, "golden", golden)) as f:
         ref = json.load(f)
     L, NT, n_rep, seed = ref["L"], ref["n_temps"], ref["n_replicas"], ref["seed"]
     beta = gi.linear_betas(*ref["T_range"], NT)
     steps, block = ref["steps"], ref["block_steps"]
-    lat, _ = _gpu_chains(L, beta, n_rep, 16, steps, ref["measure_every"], hsg.BATCHED, seed)
+    lat, _ = _gpu_chains(L, beta, n_rep, 16, steps, ref["measure_every"], hsg.BATCHED, seed,
+                         precision=ref.get("couplings", "f32"))
     lat.run_steps(steps // 2)
     lat.reset_observables()
     lat.run_steps(steps // 2)
@@ -107,6 +113,16 @@ def test_parallel_tempering_L16_matches_stored_oracle():
     ch = np.asarray(ref["chains"])                            # [chain, block, T, obs]
     cpu = ch[:, ch.shape[1] // 2:].mean(axis=1)               # equal-size blocks
     t = _t_stat(gpu, cpu)                                     # [T, obs]
+    # the per-observable agreement, printed for the record (pytest -s)
+    # (relative differences of the means at the lowest temperature; a relative
+    # difference over all temperatures would be dominated by overlaps whose
+    # means are compatible with zero)
+    g_mean, c_mean = np.mean(gpu, 0), cpu.mean(0)
+    print(f"\n{golden}: max |t| over the temperatures: e {np.abs(t[:, 0]).max():.2f}, "
+          f"q2 {np.abs(t[:, 2]).max():.2f}, q2(k_min) {np.abs(t[:, 4]).max():.2f}, q2_CG {np.abs(t[:, 5]).max():.2f}; "
+          f"relative difference of the means at T = {ref['T_range'][0]}: "
+          + ", ".join(f"{n} {abs(g_mean[-1, j] - c_mean[-1, j]) / abs(c_mean[-1, j]):.2e}"
+                      for j, n in [(0, "e"), (2, "q2"), (4, "q2(k_min)"), (5, "q2_CG")]))
     assert np.all(np.abs(t[:, 0]) < 3), t[:, 0]
     tt = t[:, [0, 2, 4, 5]]
     assert np.all(np.abs(tt) < 4), tt
