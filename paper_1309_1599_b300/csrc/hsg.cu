@@ -5,6 +5,7 @@
 // Monte Carlo step (Sec. III, App. A.1) from captured CUDA graphs.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; a no-op unless a profiler is attached
 
 #include <algorithm>
 #include <array>
@@ -71,6 +72,16 @@ struct Bucket {
 };
 
 }  // namespace
+
+// An NVTX range around a public call that enqueues device work, named after
+// the call, so a timeline profiler shows where each step's stages begin.
+// Replays of captured steps appear as the one hsg_run_steps range.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Lets the other translation units of the library report through
 // hsg_last_error().
@@ -1204,6 +1215,7 @@ static hsg_status big_stage(hsg_t h, size_t want, size_t* got) {
 }
 
 hsg_status hsg_set_couplings(hsg_t h, int sample, const float* J6) {
+  NvtxRange nvtx_range("hsg_set_couplings");
   if (!h || !J6) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   if (h->prec == HSG_BIMODAL) return fail(HSG_EINVAL, "bimodal contexts take hsg_set_couplings_bimodal");
@@ -1321,6 +1333,7 @@ hsg_status hsg_get_spins(hsg_t h, int sample, int slot, float* s_out) {
 }
 
 hsg_status hsg_set_spins_sample(hsg_t h, int sample, const float* s) {
+  NvtxRange nvtx_range("hsg_set_spins_sample");
   if (!h || !s) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   Bucket& b = h->buckets[h->sample_bucket[sample]];
@@ -1343,6 +1356,7 @@ hsg_status hsg_set_spins_sample(hsg_t h, int sample, const float* s) {
 }
 
 hsg_status hsg_get_spins_sample(hsg_t h, int sample, float* s_out) {
+  NvtxRange nvtx_range("hsg_get_spins_sample");
   if (!h || !s_out) return fail(HSG_EINVAL, "NULL argument");
   HSG_TRY(check_sample(h, sample));
   Bucket& b = h->buckets[h->sample_bucket[sample]];
@@ -1388,6 +1402,7 @@ hsg_status hsg_get_spins_device(hsg_t h, int sample, int slot, float* d_out) {
 }
 
 hsg_status hsg_sweep_hb(hsg_t h, int n) {
+  NvtxRange nvtx_range("hsg_sweep_hb");
   if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
   for (int s = 0; s < n; ++s) {
     HSG_TRY(enqueue_hb_sweep(h, h->stream));
@@ -1399,6 +1414,7 @@ hsg_status hsg_sweep_hb(hsg_t h, int n) {
 }
 
 hsg_status hsg_sweep_or(hsg_t h, int n) {
+  NvtxRange nvtx_range("hsg_sweep_or");
   if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
   if (n == 0) return HSG_OK;
   HSG_TRY(enqueue_or_sweeps(h, n, h->stream));
@@ -1410,6 +1426,7 @@ hsg_status hsg_sweep_or(hsg_t h, int n) {
 static constexpr size_t kSeqMaxSmem = 200 * 1024;
 
 hsg_status hsg_sweep_or_sequential(hsg_t h, int n) {
+  NvtxRange nvtx_range("hsg_sweep_or_sequential");
   if (!h || n < 0) return fail(HSG_EINVAL, "bad handle or n < 0");
   size_t smem_max = 0;
   for (const Bucket& b : h->buckets) {
@@ -1443,6 +1460,7 @@ hsg_status hsg_sweep_or_sequential(hsg_t h, int n) {
 }
 
 hsg_status hsg_energy(hsg_t h) {
+  NvtxRange nvtx_range("hsg_energy");
   if (!h) return fail(HSG_EINVAL, "handle is NULL");
   HSG_TRY(enqueue_energy(h, h->stream));
   h->energy_valid = true;
@@ -1466,6 +1484,7 @@ hsg_status hsg_set_energies(hsg_t h, const double* E) {
 }
 
 hsg_status hsg_pt_swap(hsg_t h) {
+  NvtxRange nvtx_range("hsg_pt_swap");
   if (!h) return fail(HSG_EINVAL, "handle is NULL");
   if (!h->energy_valid) HSG_TRY(hsg_energy(h));
   if (h->NT > 1) HSG_TRY(enqueue_pt(h, h->stream));
@@ -1512,12 +1531,14 @@ hsg_status hsg_get_pt_accepts(hsg_t h, long long* acc_out) {
 }
 
 hsg_status hsg_measure(hsg_t h) {
+  NvtxRange nvtx_range("hsg_measure");
   if (!h) return fail(HSG_EINVAL, "handle is NULL");
   if (!h->energy_valid) HSG_TRY(hsg_energy(h));
   return enqueue_measure(h, h->stream);
 }
 
 hsg_status hsg_run_steps(hsg_t h, int n_steps) {
+  NvtxRange nvtx_range("hsg_run_steps");
   if (!h || n_steps < 0) return fail(HSG_EINVAL, "bad handle or n_steps < 0");
   if (n_steps == 0) return HSG_OK;
   if (h->persistent) {
@@ -1562,6 +1583,7 @@ hsg_status hsg_run_steps(hsg_t h, int n_steps) {
 }
 
 hsg_status hsg_read_observables(hsg_t h, double* obs_out, long long* counts_out) {
+  NvtxRange nvtx_range("hsg_read_observables");
   if (!h || !obs_out) return fail(HSG_EINVAL, "NULL argument");
   const size_t n = static_cast<size_t>(h->S) * h->NT;
   HSG_CUDA(cudaMemcpyAsync(obs_out, h->d_obs, sizeof(double) * n * HSG_NOBS, cudaMemcpyDeviceToHost, h->stream));
@@ -1907,6 +1929,7 @@ hsg_status tune_pair(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1) {
 extern "C" {
 
 hsg_status hsg_autotune(hsg_t h) {
+  NvtxRange nvtx_range("hsg_autotune");
   if (!h) return fail(HSG_EINVAL, "handle is NULL");
   HSG_CUDA(cudaStreamSynchronize(h->stream));
   HSG_TRY(status_check(h));
