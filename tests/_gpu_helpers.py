@@ -55,15 +55,16 @@ def colours(L):
     return (i % L + (i // L) % L + i // (L * L)) % 2
 
 
-def compare_sweep(lat, J, before, after, kind, hb_t, J9s=None):
+def compare_sweep(lat, J, before, after, kind, hb_t, J9s=None, tmp=None):
     """Per-half-sweep parity of one GPU sweep: the black half against the
     oracle's black half from `before`; the white half against the oracle's
     white half applied to the GPU's new black spins.  J: couplings per sample
     as given to the library, or J9s: the oracle's own bond matrices per
-    sample (bimodal couplings).  Returns (max |ds| over all compared
-    components, number of frame-ambiguous sites, max |du| over those
-    sites)."""
-    tmp = temp_of(lat)
+    sample (bimodal couplings).  tmp: the temperature index of each slot
+    during the sweep (default: the context's current labels).  Returns (max
+    |ds| over all compared components, number of frame-ambiguous sites, max
+    |du| over those sites)."""
+    tmp = temp_of(lat) if tmp is None else tmp
     worst, n_amb, worst_u = 0.0, 0, 0.0
     for s, L in enumerate(lat.Ls):
         J9 = J9s[s] if J9s is not None else oracle.j9_from_j6(J[s])

@@ -6,7 +6,7 @@ import pytest
 import hsg_inputs as gi
 import oracle
 import paper_1309_1599_b300 as hsg
-from _gpu_helpers import make, state
+from _gpu_helpers import SWEEP_TOL, compare_sweep, make, state, temp_of
 
 pytestmark = pytest.mark.gpu
 
@@ -116,6 +116,39 @@ def test_joint_launch_refused_when_sets_cannot_be_held_whole():
     with pytest.raises(hsg.HsgError, match="whole"):
         hsg.Lattice([16, 8], gi.linear_betas(0.2, 1.2, 8), n_replicas=2, coupling_prec=hsg.F16,
                     layout=hsg.BATCHED, persistent=2)
+
+
+@pytest.mark.parametrize("Ls,prec,layout,persistent", [([8, 12], hsg.F16, hsg.BATCHED, 1),
+                                                      ([12, 8], hsg.F32, hsg.BATCHED, 2),
+                                                      ([8], hsg.F32, hsg.PLAIN, 1)])
+def test_resident_step_matches_oracle_per_half_sweep(Ls, prec, layout, persistent):
+    """The resident kernel checked against the oracle directly, not through
+    the streaming path: one resident step of heat-bath sweeps only
+    (n_or = 0), per half-sweep from the GPU's state before the step (every
+    site within 2e-5; frame-ambiguous sites on u and the norm), then the
+    labels the kernel's in-kernel PT sweep left against the oracle's PT
+    sweep on the kernel's energies, and those energies against the oracle's
+    energy of the new spins."""
+    betas = gi.linear_betas(0.4, 1.5, 4)
+    lat, J = make(Ls, betas, n_rep=2, prec=prec, layout=layout, n_or=0, measure_every=0, persistent=persistent)
+    lat.run_steps(20)                            # away from the initial state
+    before, tmp, perm0 = state(lat), temp_of(lat), lat.get_perm().copy()
+    hb_t, pt_t, _ = (int(x) for x in lat.get_counters())
+    lat.run_steps(1)
+    after = state(lat)
+    worst, n_amb, worst_u = compare_sweep(lat, J, before, after, oracle.HB, hb_t, tmp=tmp)
+    assert worst <= SWEEP_TOL and worst_u <= SWEEP_TOL, (worst, worst_u)
+    assert n_amb <= 1e-3 * sum(L ** 3 for L in Ls) * lat.R + 6
+    E = lat.get_energies()
+    for s, L in enumerate(Ls):
+        J9 = oracle.j9_from_j6(J[s])
+        for slot in range(lat.R):
+            ref = oracle.energy(L, J9, after[s][slot])
+            assert abs(E[s, slot] - ref) <= 2e-6 * abs(ref), (s, slot, E[s, slot], ref)
+        for r in range(lat.n_replicas):
+            p = perm0[s, r].copy()
+            oracle.pt_sweep(betas, E[s], p, lat.seed, s * lat.n_replicas + r, pt_t)
+            assert np.array_equal(lat.get_perm()[s, r], p), (s, r)
 
 
 def test_persistent_step_matches_oracle_step_from_equilibrium():
