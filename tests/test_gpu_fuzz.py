@@ -72,6 +72,14 @@ def test_random_configurations_agree_across_step_kernels(seed):
         res = None                          # a lattice group too large for shared memory
     if res is not None:
         runs["resident"] = _result(res, steps)
+    if len(c["Ls"]) == 2:
+        try:
+            joint = _make(c, persistent=2)
+        except hsg.HsgError:
+            joint = None                    # replica sets that cannot be held whole
+        if joint is not None:
+            assert joint.get_resident_plan(0)["one_launch"]
+            runs["joint"] = _result(joint, steps)
     ref = runs["fused"]
     for name, r in runs.items():
         assert all(np.array_equal(x, y) for rx, ry in zip(ref[0], r[0]) for x, y in zip(rx, ry)), (name, c)
@@ -120,14 +128,19 @@ TILINGS_GP2 = [(L, B) for L, B in TILINGS if _ring_bytes(L, B, 2) <= 200 * 1024
                and (L if B == L else B + 2) * (L // 2) <= 384]
 
 
-@pytest.mark.parametrize("L,band", TILINGS_GP2, ids=[f"L{L}_b{B}" for L, B in TILINGS_GP2])
-def test_two_groups_per_thread_equal_the_two_pass_sweep(L, band):
+GP2_CASES = [(L, B, hsg.F16) for L, B in TILINGS_GP2] + [(16, 16, hsg.F32), (64, 8, hsg.F32), (20, 20, hsg.BIMODAL),
+                                                      (32, 8, hsg.BIMODAL)]
+
+
+@pytest.mark.parametrize("L,band,prec", GP2_CASES,
+                         ids=[f"L{L}_b{B}_p{p}" for L, B, p in GP2_CASES])
+def test_two_groups_per_thread_equal_the_two_pass_sweep(L, band, prec):
     """Two lattice groups per thread (each coupling loaded and converted once
     for four lattices), at each band height whose ring fits: the two-pass
     kernel's spins bit for bit over heat-bath and overrelaxation sweeps, the
     same labels and acceptances, and the energies of one group per thread in
     the same bands exactly (the same partial sums in the same order)."""
-    c = dict(Ls=[L, L], betas=[0.7, 1.9], n_rep=2, layout=hsg.BATCHED, prec=hsg.F16, n_or=2, me=0)
+    c = dict(Ls=[L, L], betas=[0.7, 1.9], n_rep=2, layout=hsg.BATCHED, prec=prec, n_or=2, me=0)
     a = _make(c, band_rows=band, fused_groups=2)
     plan = a.get_sweep_plan(0)
     assert plan["fused"] and plan["band_rows"] == band
