@@ -88,17 +88,17 @@ RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
     # the L=64 overrelaxation sweep in 8-row bands: 388.0 MB for one sample of
     # 64 lattices, x8 samples
-    ("f337c22e34aed967", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3103889408,
+    ("0b00f107ce937a92", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3103889408,
     # the same sweep of the plain FP32 form (one lattice per element): 418.4 MB
     # for one sample, x8 samples; the 64 lattices of a sample read their
     # shared couplings through L2, so this is far below the 96 B per update
     # that lattices with couplings of their own move
-    ("f337c22e34aed967", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
+    ("0b00f107ce937a92", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
     # the L=32 overrelaxation sweep: one launch of 64 samples x 48 lattices
-    ("f337c22e34aed967", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
+    ("0b00f107ce937a92", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
     # the resident steps of 256 x L=8 + 256 x L=12 samples, both sizes in one
     # launch of 10 MCS: 249.1 MB read + 160.8 MB written
-    ("570957506790d731", "L8x256_L12x256_R32_f16",
+    ("6647467fc9aaf555", "L8x256_L12x256_R32_f16",
      "k_persistent_pair<2,f16> (10 MCS per launch, both lattice sizes in one launch)"): 409880064,
 }
 

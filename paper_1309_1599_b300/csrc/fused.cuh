@@ -3,8 +3,9 @@
 // spins, white half with the new black spins), reading each spin once from
 // HBM and writing it once.
 //
-// A CTA owns one lattice group (V lattices of one sample) and a band of
-// `band_rows` rows y (all x), and marches through the planes z.  At step z it
+// A CTA owns one lattice group (V lattices of one sample; or GP groups, each
+// thread updating its sites in all of them) and a band of `band_rows` rows y
+// (all x), and marches through the planes z.  At step z it
 // updates the black sites of plane z and then the white sites of plane z-1:
 // black(z) needs the white spins of planes z-1, z, z+1 before they change,
 // white(z-1) needs the black spins of planes z-2, z-1, z after they changed.

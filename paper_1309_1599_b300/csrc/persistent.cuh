@@ -1,15 +1,17 @@
 // Shared-memory-resident Monte Carlo of small lattices: one launch runs K
 // whole Monte Carlo steps (Sec. III: heat-bath sweep, overrelaxation sweeps,
 // energies, one parallel-tempering sweep) for every replica set of the
-// samples of one L, with the spins of a replica set held in shared memory
-// from the first step to the last.
+// samples of one L (k_persistent), or of two lattice sizes at once
+// (k_persistent_pair), with the spins held in shared memory from the first
+// step to the last.
 //
-// A CTA owns one replica set: the N_T lattices of one replica index of one
-// sample (all temperatures).  Parallel tempering only exchanges temperatures
-// inside a replica set (App. A.1), so each CTA runs its own PT sweep after its
-// own energies; no CTA ever waits for another.  Where a whole set does not
-// fit (L = 16 to 24), a CTA holds G_sub of its lattice groups for one step:
-// the launch writes their energies and the caller runs the PT sweep.
+// A CTA owns one replica set -- the N_T lattices of one replica index of one
+// sample (all temperatures) -- or several whole replica sets of one sample.
+// Parallel tempering only exchanges temperatures inside a replica set
+// (App. A.1), so each CTA runs the PT sweeps of its own sets after their
+// energies; no CTA ever waits for another.  Where a whole set does not fit
+// (L = 16 to 24), a CTA holds G_sub of its lattice groups for one step: the
+// launch writes their energies and the caller runs the PT sweep.
 //
 // Shared-memory layout.  Global memory keeps each row's sites split by x
 // parity (the streaming kernels' order).  In shared memory the sites are split
