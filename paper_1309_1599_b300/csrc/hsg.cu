@@ -125,6 +125,8 @@ struct hsg_ctx {
   bool pair_special = false;   // joint launch: the L = 12 with L = 8 specialisation
   int pair_threads = 0;        // joint launch: threads per CTA
   size_t pair_smem = 0;        // joint launch: dynamic shared memory per CTA
+  std::vector<std::array<int, 2>> pair_cands;  // joint launch: feasible (sets per CTA, bond
+                                               // residency) of the smaller size, planned first
   long long timeout_cycles = 0;
   int sweep_kernel = 0;
   uint64_t launches = 0;       // kernels enqueued by this context so far
@@ -625,27 +627,32 @@ hsg_status plan_joint(hsg_ctx* h) {
   std::vector<int> jsbs;
   if (special && h->prec != HSG_F32) jsbs.push_back(2);
   jsbs.push_back(special ? 1 : 0);
-  int best_k = 0, best_jsb = 0;
-  size_t best_smem = 0;
-  for (int k = h->n_rep; k >= 1 && best_k == 0; --k) {
+  // every (sets per CTA, bond residency) of bucket b that fits in the shared
+  // memory bucket a's CTAs take; the first (most sets, FP32 bonds first) is
+  // the plan until the autotuner times the others
+  h->pair_cands.clear();
+  for (int k = h->n_rep; k >= 1; --k) {
     if (h->n_rep % k != 0 || k * h->NT > kMaxTempsResident) continue;
     for (const int jsb : jsbs) {
       const size_t smem_b =
           static_cast<size_t>(12) * h->V * k * G_set * B.N + 3 * static_cast<size_t>(B.N) * bond_bytes[jsb];
-      if (smem_b > smem_a) continue;  // bucket a's CTAs set the launch's shared memory
-      best_k = k;
-      best_jsb = jsb;
-      best_smem = smem_a;
-      break;
+      if (smem_b <= smem_a) h->pair_cands.push_back({k, jsb});
     }
   }
-  if (best_k == 0) return fail(HSG_EINVAL, "no joint resident plan for these lattice sizes");
+  if (h->pair_cands.empty()) return fail(HSG_EINVAL, "no joint resident plan for these lattice sizes");
+  const int best_k = h->pair_cands[0][0], best_jsb = h->pair_cands[0][1];
+  const size_t best_smem = smem_a;
+  for (const auto& c : h->pair_cands) {
+    void* f = pair_kernel(h->V, h->prec, special, c[1]);
+    cudaFuncAttributes fc;
+    HSG_CUDA(cudaFuncGetAttributes(&fc, f));
+    if (best_smem + fc.sharedSizeBytes > static_cast<size_t>(optin))
+      return fail(HSG_EINVAL, "a replica set of L = " + std::to_string(A.L) + " does not fit one CTA of the joint launch");
+    HSG_TRY(raise_smem_limit(f, static_cast<size_t>(optin) - fc.sharedSizeBytes));
+  }
   void* fn = pair_kernel(h->V, h->prec, special, best_jsb);
   cudaFuncAttributes fa;
   HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
-  if (best_smem + fa.sharedSizeBytes > static_cast<size_t>(optin))
-    return fail(HSG_EINVAL, "a replica set of L = " + std::to_string(A.L) + " does not fit one CTA of the joint launch");
-  HSG_TRY(raise_smem_limit(fn, static_cast<size_t>(optin) - fa.sharedSizeBytes));
   const int threads = std::min(fa.maxThreadsPerBlock, std::max(A.res_threads, B.res_threads)) / 32 * 32;
   int occ = 0;
   HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, best_smem));
@@ -697,11 +704,13 @@ PersistentParams persistent_params(hsg_ctx* h, const Bucket& b, int steps) {
   p.G_sub = b.res_gsub;
   p.sets = b.res_sets;
   p.pt = h->res_split ? 0 : 1;
+  p.warps = b.res_threads / 32;
   return p;
 }
 
 hsg_status launch_persistent(hsg_ctx* h, const Bucket& b, PersistentParams p, int gp, int threads,
                              cudaStream_t st) {
+  p.warps = threads / 32;
   void* args[] = {&p};
   *h->launch_sink += 1;
   const int n_sub = h->NT / h->V / p.G_sub;  // CTAs per replica set
@@ -1857,15 +1866,21 @@ hsg_status tune_persistent(hsg_ctx* h, Bucket& b, cudaEvent_t e0, cudaEvent_t e1
 hsg_status tune_pair(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1) {
   Bucket& A = h->buckets[h->pair_a];
   Bucket& B = h->buckets[h->pair_b];
-  const std::array<int, 6> key = {2, A.L * 1024 + B.L, h->V, h->prec, h->NT * 256 + B.res_sets, B.res_js};
+  const int G_set = h->NT / h->V;
+  auto set_b = [&](int k, int jsb) {
+    B.res_sets = k;
+    B.res_gsub = k * G_set;
+    B.res_js = jsb;
+  };
+  const std::array<int, 6> key = {2, A.L * 1024 + B.L, h->V, h->prec, h->NT * 256 + h->n_rep, 0};
   std::array<int, 3> got;
   if (tune_lookup(key, &got)) {
-    h->pair_threads = A.res_threads = B.res_threads = got[1];
+    set_b(got[0] >> 2, got[0] & 3);
+    A.res_threads = got[1];
+    B.res_threads = got[2];
+    h->pair_threads = std::max(got[1], got[2]);
     return HSG_OK;
   }
-  void* fn = pair_kernel(h->V, h->prec, h->pair_special, B.res_js);
-  cudaFuncAttributes fa;
-  HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
   const size_t S = h->S;
   const size_t na = static_cast<size_t>(A.S_b) * h->R * 3 * A.N, nb = static_cast<size_t>(B.S_b) * h->R * 3 * B.N;
   float *spa = nullptr, *spb = nullptr;
@@ -1893,24 +1908,50 @@ hsg_status tune_pair(hsg_ctx* h, cudaEvent_t e0, cudaEvent_t e1) {
     }
     pa.spins = spa;
     pb.spins = spb;
+    // candidates: bucket b's (sets per CTA, bond residency) and each
+    // bucket's warps; the launch takes the larger warp count, and the
+    // other bucket's surplus warps sit out its sweeps.  The current plan
+    // first, so that ties keep it.
     float best_ms = -1.0f;
-    int best = h->pair_threads;
-    std::vector<int> cands = {h->pair_threads};  // the current plan first
-    for (const int W : {16, 18, 20}) if (32 * W != h->pair_threads) cands.push_back(32 * W);
-    for (const int t : cands) {
+    std::array<int, 4> best = {B.res_sets, B.res_js, A.res_threads, B.res_threads};
+    std::vector<std::array<int, 4>> cands = {best};
+    for (const auto& c : h->pair_cands)
+      for (const int ta : {512, 576})
+        for (const int tb : {512, 576, 640}) {
+          const std::array<int, 4> cand = {c[0], c[1], ta, tb};
+          if (cand != best) cands.push_back(cand);
+        }
+    for (const auto& c : cands) {
+      const int t = std::max(c[2], c[3]);
+      void* fn = pair_kernel(h->V, h->prec, h->pair_special, c[1]);
+      cudaFuncAttributes fa;
+      HSG_CUDA(cudaFuncGetAttributes(&fa, fn));
       if (t > fa.maxThreadsPerBlock) continue;
       int occ = 0;
       HSG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, h->pair_smem));
       if (occ < 1) continue;
+      set_b(c[0], c[1]);
+      PersistentParams qb = persistent_params(h, B, pb.steps);
+      qb.spins = spb;
+      qb.perm = perm;
+      qb.temp_of = temp_of;
+      qb.E = E;
+      qb.accepted = acc;
+      PersistentParams qa = pa;
+      qa.warps = c[2] / 32;
+      qb.warps = c[3] / 32;
       float ms = 0.0f;
-      HSG_TRY(time_ms(h, e0, e1, 2, [&]() { return launch_pair(h, pa, pb, t, h->stream); }, &ms));
+      HSG_TRY(time_ms(h, e0, e1, 2, [&]() { return launch_pair(h, qa, qb, t, h->stream); }, &ms));
       if (best_ms < 0.0f || ms < 0.98f * best_ms) {
         best_ms = ms;
-        best = t;
+        best = c;
       }
     }
-    h->pair_threads = A.res_threads = B.res_threads = best;
-    tune_store(key, {0, best, 0});
+    set_b(best[0], best[1]);
+    A.res_threads = best[2];
+    B.res_threads = best[3];
+    h->pair_threads = std::max(best[2], best[3]);
+    tune_store(key, {(best[0] << 2) | best[1], best[2], best[3]});
     return HSG_OK;
   };
   if (st == HSG_OK) st = run();

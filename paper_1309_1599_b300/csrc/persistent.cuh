@@ -85,6 +85,8 @@ struct PersistentParams {
                            // sets * N_T <= kMaxTempsResident), 1 for parts of a set
   int pt;                  // 1: PT in the kernel (whole sets); 0: one step per
                            // launch, energies out, the PT sweep by the caller
+  int warps;               // warps that sweep (<= the block's); the others only
+                           // copy in and out and join the barriers
 };
 
 // The CTA-wide tables of a resident CTA, indexed by local lattice (the
@@ -283,13 +285,13 @@ struct ResidentWarps {
   int sub;    // this warp's index within its group
 };
 
-__device__ __forceinline__ ResidentWarps resident_warps(int G_set) {
-  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+__device__ __forceinline__ ResidentWarps resident_warps(int G_set, int W) {
+  const int warp = threadIdx.x >> 5;
   ResidentWarps rw;
   rw.wpg = W >= G_set ? W / G_set : 1;
   rw.gpp = W / rw.wpg;
-  rw.g0 = warp / rw.wpg;
-  rw.sub = warp - rw.g0 * rw.wpg;
+  rw.g0 = warp < W ? warp / rw.wpg : rw.gpp;  // warps beyond W sit out the sweeps
+  rw.sub = warp - (warp < W ? rw.g0 : 0) * rw.wpg;
   return rw;
 }
 
@@ -418,7 +420,7 @@ __device__ __forceinline__ void persistent_body(const PersistentParams& p, const
   const uint32_t lat_base = static_cast<uint32_t>(sg) * p.R + static_cast<uint32_t>(loc0);
   const uint32_t t_hb0 = p.counters[0], t_pt0 = p.counters[1];
   const int G_set = G_sub;                                // groups swept by this CTA
-  const ResidentWarps rw = resident_warps(G_set / GP);
+  const ResidentWarps rw = resident_warps(G_set / GP, min(p.warps, static_cast<int>(blockDim.x >> 5)));
 
   // replica set -> shared memory, parity-split rows -> colour split; one
   // element = the V interleaved lattices of a site
