@@ -183,7 +183,11 @@ class Lattice:
     """One libhsg context: S samples x n_replicas x n_temps lattices.
 
     ``Lattice(L, beta, n_replicas, ...)`` is hsg_lattice_create; L is an int
-    or a list of per-sample sizes."""
+    or a list of per-sample sizes.  The keyword arguments are the fields of
+    hsg_config in include/hsg.h: among them ``persistent`` (False/0 streaming
+    steps, True/1 resident steps with one launch per lattice size, 2 all
+    lattice sizes in one launch) and the tiling overrides ``band_rows`` and
+    ``fused_groups`` (0 leaves both to the library and its autotuner)."""
 
     def __init__(self, L, beta, n_replicas=2, n_samples=None, coupling_prec=F32,
                  layout=PLAIN, n_or=8, measure_every=0, seed=1, stream=None,
