@@ -232,6 +232,34 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
     assert np.array_equal(a.get_counters(), b.get_counters())
 
 
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_checkpoint_resume_bit_identical_with_resident_steps(tmp_path, persistent):
+    """Save a mixed-size context running resident steps (one launch per size,
+    or both sizes in one launch) and resume it in a fresh context of the same
+    shape, which may even use the other resident mode: the continued run
+    equals the uninterrupted one bit for bit (spins, labels, acceptances,
+    observables, counters)."""
+    betas = gi.linear_betas(0.3, 1.2, 8)
+    a, _ = make([12, 8], betas, n_rep=2, prec=hsg.F16, layout=hsg.BATCHED, n_or=2, measure_every=2,
+                persistent=persistent)
+    a.run_steps(4)
+    path = str(tmp_path / "ck_res.bin")
+    a.save(path)
+    a.run_steps(4)
+    other = 3 - persistent
+    b = hsg.Lattice([12, 8], betas, n_replicas=2, coupling_prec=hsg.F16, layout=hsg.BATCHED, n_or=2,
+                    measure_every=2, seed=a.seed, persistent=other)
+    b.load(path)
+    b.run_steps(4)
+    assert all(np.array_equal(x, y) for rx, ry in zip(state(a), state(b)) for x, y in zip(rx, ry))
+    assert np.array_equal(a.get_perm(), b.get_perm())
+    assert np.array_equal(a.get_pt_accepts(), b.get_pt_accepts())
+    assert np.array_equal(a.get_counters(), b.get_counters())
+    oa, ca = a.read_observables()
+    ob, cb = b.read_observables()
+    assert np.array_equal(ca, cb) and np.allclose(oa, ob, rtol=1e-9, atol=1e-12)
+
+
 def test_mismatched_checkpoint_rejected(tmp_path):
     a, _ = make([8], [1.0], n_rep=2)
     path = str(tmp_path / "ck.bin")
