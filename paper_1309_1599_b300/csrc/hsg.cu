@@ -618,38 +618,56 @@ hsg_status plan_joint(hsg_ctx* h) {
   const int ia = h->buckets[0].N >= h->buckets[1].N ? 0 : 1, ib = 1 - ia;
   Bucket& A = h->buckets[ia];
   Bucket& B = h->buckets[ib];
-  const bool special = (h->V == 2 && A.L == 12 && B.L == 8);
   const size_t stored = h->prec == HSG_F16 ? 12 : h->prec == HSG_BIMODAL ? 1 : 24;
   const size_t bond_bytes[3] = {0, stored, 24};
   const int G_set = h->NT / h->V;
-  const int jsa = special ? 1 : 0;
-  const size_t smem_a = static_cast<size_t>(12) * h->V * G_set * A.N + 3 * static_cast<size_t>(A.N) * bond_bytes[jsa];
-  std::vector<int> jsbs;
-  if (special && h->prec != HSG_F32) jsbs.push_back(2);
-  jsbs.push_back(special ? 1 : 0);
-  // every (sets per CTA, bond residency) of bucket b that fits in the shared
-  // memory bucket a's CTAs take; the first (most sets, FP32 bonds first) is
-  // the plan until the autotuner times the others
-  h->pair_cands.clear();
-  for (int k = h->n_rep; k >= 1; --k) {
-    if (h->n_rep % k != 0 || k * h->NT > kMaxTempsResident) continue;
-    for (const int jsb : jsbs) {
-      const size_t smem_b =
-          static_cast<size_t>(12) * h->V * k * G_set * B.N + 3 * static_cast<size_t>(B.N) * bond_bytes[jsb];
-      if (smem_b <= smem_a) h->pair_cands.push_back({k, jsb});
+  // The L = 12 with L = 8 specialisation keeps bucket a's bonds resident as
+  // stored; where that does not fit one CTA (FP32 bonds beside eight
+  // temperatures of spins), or for other sizes, the generic joint kernel
+  // reads the bonds from global memory.
+  bool special = false;
+  size_t smem_a = 0;
+  int jsa = 0;
+  for (const bool sp : {h->V == 2 && A.L == 12 && B.L == 8, false}) {
+    jsa = sp ? 1 : 0;
+    smem_a = static_cast<size_t>(12) * h->V * G_set * A.N + 3 * static_cast<size_t>(A.N) * bond_bytes[jsa];
+    std::vector<int> jsbs;
+    if (sp && h->prec != HSG_F32) jsbs.push_back(2);
+    jsbs.push_back(sp ? 1 : 0);
+    // every (sets per CTA, bond residency) of bucket b that fits in the
+    // shared memory bucket a's CTAs take; the first (most sets, FP32 bonds
+    // first) is the plan until the autotuner times the others
+    h->pair_cands.clear();
+    for (int k = h->n_rep; k >= 1; --k) {
+      if (h->n_rep % k != 0 || k * h->NT > kMaxTempsResident) continue;
+      for (const int jsb : jsbs) {
+        const size_t smem_b =
+            static_cast<size_t>(12) * h->V * k * G_set * B.N + 3 * static_cast<size_t>(B.N) * bond_bytes[jsb];
+        if (smem_b <= smem_a) h->pair_cands.push_back({k, jsb});
+      }
     }
+    bool fits = !h->pair_cands.empty();
+    for (const auto& c : h->pair_cands) {
+      cudaFuncAttributes fc;
+      HSG_CUDA(cudaFuncGetAttributes(&fc, pair_kernel(h->V, h->prec, sp, c[1])));
+      if (smem_a + fc.sharedSizeBytes > static_cast<size_t>(optin)) fits = false;
+    }
+    if (fits) {
+      special = sp;
+      break;
+    }
+    h->pair_cands.clear();
   }
-  if (h->pair_cands.empty()) return fail(HSG_EINVAL, "no joint resident plan for these lattice sizes");
-  const int best_k = h->pair_cands[0][0], best_jsb = h->pair_cands[0][1];
-  const size_t best_smem = smem_a;
+  if (h->pair_cands.empty())
+    return fail(HSG_EINVAL, "a replica set of L = " + std::to_string(A.L) + " does not fit one CTA of the joint launch");
   for (const auto& c : h->pair_cands) {
     void* f = pair_kernel(h->V, h->prec, special, c[1]);
     cudaFuncAttributes fc;
     HSG_CUDA(cudaFuncGetAttributes(&fc, f));
-    if (best_smem + fc.sharedSizeBytes > static_cast<size_t>(optin))
-      return fail(HSG_EINVAL, "a replica set of L = " + std::to_string(A.L) + " does not fit one CTA of the joint launch");
     HSG_TRY(raise_smem_limit(f, static_cast<size_t>(optin) - fc.sharedSizeBytes));
   }
+  const int best_k = h->pair_cands[0][0], best_jsb = h->pair_cands[0][1];
+  const size_t best_smem = smem_a;
   void* fn = pair_kernel(h->V, h->prec, special, best_jsb);
   cudaFuncAttributes fa;
   HSG_CUDA(cudaFuncGetAttributes(&fa, fn));

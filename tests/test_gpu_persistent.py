@@ -69,6 +69,9 @@ JOINT = [
     ([8, 12], 4, 2, hsg.F32, hsg.BATCHED, 4),
     ([6, 10, 6], 4, 2, hsg.F16, hsg.PLAIN, 4),
     ([10, 4], 6, 3, hsg.F32, hsg.BATCHED, 4),
+    # L = 12 with FP32 bonds and 8 temperatures: too large for the
+    # specialisation's resident bonds, so the generic joint kernel takes it
+    ([12, 8], 8, 2, hsg.F32, hsg.BATCHED, 4),
 ]
 
 
