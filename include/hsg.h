@@ -133,7 +133,8 @@ typedef struct {
                              every replica set held whole (HSG_EINVAL
                              otherwise); specialised for L = 12 with L = 8 in
                              the batched layout, generic (bonds read from
-                             global memory) for other pairs.
+                             global memory) for other pairs; more than two
+                             lattice sizes are refused (HSG_EINVAL).
                              0: streaming steps. */
   double bimodal_D;       /* HSG_BIMODAL: the magnitude D >= 0 of the
                              anisotropic couplings (the paper uses 0.5 and 1);

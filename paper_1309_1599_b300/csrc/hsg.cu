@@ -609,7 +609,8 @@ hsg_status plan_persistent(hsg_ctx* h) {
 // launch's one block shape and shared-memory size serve both.  HSG_EINVAL if
 // a replica set cannot be held whole or the buckets do not fit.
 hsg_status plan_joint(hsg_ctx* h) {
-  if (h->buckets.size() != 2) return HSG_OK;  // one lattice size: one launch already
+  if (h->buckets.size() == 1) return HSG_OK;  // one lattice size: one launch already
+  if (h->buckets.size() > 2) return fail(HSG_EINVAL, "one resident launch holds at most two lattice sizes");
   if (h->res_split)
     return fail(HSG_EINVAL, "one launch for all lattice sizes needs every replica set held whole by a CTA");
   int dev = 0, optin = 0;

@@ -54,6 +54,7 @@ def _cfg(**kw):
     c.band_rows = kw.pop("band_rows", 0)
     c.persistent = kw.pop("persistent", 0)
     c.bimodal_D = kw.pop("bimodal_D", 1.0)
+    c.fused_groups = kw.pop("fused_groups", 0)
     return c, (L, beta)
 
 
@@ -70,6 +71,11 @@ def _cfg(**kw):
     (dict(persistent=1, layout=1, beta=[1.0, 2.0, 3.0], n_replicas=2), "multiple"),
     (dict(prec=2, bimodal_D=-0.5), "bimodal_D"),
     (dict(prec=2, bimodal_D=float("nan")), "bimodal_D"),
+    (dict(persistent=3), "persistent"),
+    (dict(fused_groups=3), "fused_groups"),
+    (dict(fused_groups=1, sweep_kernel=1), "fused_groups"),
+    (dict(fused_groups=2, layout=0), "fused_groups"),
+    (dict(fused_groups=2, layout=1, n_replicas=1, beta=[1.0, 2.0]), "fused_groups"),
 ])
 def test_invalid_configs_rejected_on_host(lib, kw, msg):
     c, keep = _cfg(**kw)

@@ -115,9 +115,13 @@ def test_joint_launch_of_two_lattice_sizes_equals_streaming(case):
 
 def test_joint_launch_refused_when_sets_cannot_be_held_whole():
     """persistent = 2 needs every replica set held whole by one CTA: L = 16
-    with 8 temperatures splits its sets (393 KB), so the context is refused."""
+    with 8 temperatures splits its sets (393 KB), so the context is refused;
+    so is a context with three lattice sizes."""
     with pytest.raises(hsg.HsgError, match="whole"):
         hsg.Lattice([16, 8], gi.linear_betas(0.2, 1.2, 8), n_replicas=2, coupling_prec=hsg.F16,
+                    layout=hsg.BATCHED, persistent=2)
+    with pytest.raises(hsg.HsgError, match="two lattice sizes"):
+        hsg.Lattice([4, 6, 8], gi.linear_betas(0.2, 1.2, 2), n_replicas=2, coupling_prec=hsg.F16,
                     layout=hsg.BATCHED, persistent=2)
 
 
