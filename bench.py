@@ -57,6 +57,10 @@ WORKLOADS = {
     # inputs (each lattice with its own copy of its sample's couplings)
     "L64_S512_R1_f32_plain": dict(L=64, S=512, n_rep=1, NT=1, Tmin=0.5, Tmax=0.5, n_or=8, measure_every=10,
                                   prec="f32", layout="plain"),
+    # profiling size of the plain single-lattice form: 16 lattices of L=64,
+    # each with FP32 couplings of its own (302 MB of couplings, above L2)
+    "L64_S16_R1_f32_plain": dict(L=64, S=16, n_rep=1, NT=1, Tmin=0.5, Tmax=0.5, n_or=8, measure_every=10,
+                                 prec="f32", layout="plain"),
     # profiling size: 512 lattices of L=32 (201 MB of spins, above L2)
     "L32_S8_R64_f16": dict(L=32, S=8, n_rep=2, NT=32, Tmin=0.15, Tmax=0.75, n_or=8,
                            measure_every=10),
@@ -94,6 +98,12 @@ NCU_TRAFFIC = {
     # shared couplings through L2, so this is far below the 96 B per update
     # that lattices with couplings of their own move
     ("0b00f107ce937a92", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
+    # the plain single-lattice form (FP32 couplings of its own per lattice):
+    # 365.0 MB read + 42.6 MB written for 16 lattices (97.2 B per update
+    # against the algorithmic 96), x32 for the 512 lattices timed beside the
+    # default workload
+    ("0b00f107ce937a92", "L64_S16_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 407521536,
+    ("0b00f107ce937a92", "L64_S512_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 13040689152,
     # the L=32 overrelaxation sweep: one launch of 64 samples x 48 lattices
     ("0b00f107ce937a92", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
     # the resident steps of 256 x L=8 + 256 x L=12 samples, both sizes in one
@@ -117,6 +127,13 @@ def workload_form(hsg, w):
 
 def spin_bytes(w):
     return 12 * w["n_rep"] * w["NT"] * sum(L ** 3 for L in sample_Ls(w))
+
+
+def coupling_bytes(w):
+    """Device bytes of the workload's couplings (one set per sample: 16 B per
+    bond for FP16 as stored, 24 B for FP32)."""
+    per_bond = 16 if w.get("prec", "f16") == "f16" else 24
+    return 3 * per_bond * sum(L ** 3 for L in sample_Ls(w))
 
 
 def kernel_source_hash(files=FUSED_SOURCES) -> str:
@@ -620,6 +637,8 @@ def workload_config(name, w, world):
             "l2": ("no flush: spins stay in shared memory within a launch; "
                    f"the whole set ({spin_bytes(w) / 1e6:.0f} MB per GPU) exceeds L2" if persistent else
                    "no flush: spins per GPU exceed L2 (126 MB)" if spin_bytes(w) > 126e6 else
+                   f"no flush: spins and couplings per GPU ({(spin_bytes(w) + coupling_bytes(w)) / 1e6:.0f} MB) "
+                   "exceed L2 (126 MB)" if spin_bytes(w) + coupling_bytes(w) > 126e6 else
                    f"no flush: the whole state ({spin_bytes(w) / 1e3:.0f} KB of spins) stays in L2 in any "
                    "run of this size; the workload is latency-bound and not graded against HBM"),
             "resident": bool(persistent),

@@ -71,3 +71,8 @@ def test_workload_forms():
     assert bench.workload_form(H, bench.WORKLOADS["L16_S1_R32_f32"]) == (H.F32, H.BATCHED)
     assert bench.workload_form(H, bench.WORKLOADS[bench.DEFAULT_WORKLOAD]) == (H.F16, H.BATCHED)
     assert bench.spin_bytes(bench.WORKLOADS["L8_S1_R2_f32"]) == 12 * 2 * 512
+    # couplings: one set per sample, 24 B per FP32 bond and 16 B per FP16 bond as stored
+    assert bench.coupling_bytes(bench.WORKLOADS["L64_S16_R1_f32_plain"]) == 16 * 3 * 24 * 64 ** 3
+    assert bench.coupling_bytes(bench.WORKLOADS["L64_S8_R64_f16"]) == 8 * 3 * 16 * 64 ** 3
+    assert "couplings" in bench.workload_config("L64_S16_R1_f32_plain",
+                                                bench.WORKLOADS["L64_S16_R1_f32_plain"], 1)["l2"]
