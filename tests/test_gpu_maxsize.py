@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import paper_1309_1599_b300 as hsg
+from _gpu_helpers import frame_ambiguous_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +61,9 @@ def test_largest_lattice_sampled_half_sweep_parity(kind):
         nb_state = s0 if c == 0 else s1
         ref, h = _site_update(int(i), bits, nb_state, s0, kind, beta, 0, t)
         if kind == oracle.HB and abs(h[2]) < 1e-4 * np.linalg.norm(h):
-            n_amb += 1               # frame-ambiguous (field at the equator)
+            n_amb += 1               # frame-ambiguous (field at the equator): either frame
+            d = frame_ambiguous_diff(s1[i][None].astype(np.float64), ref[None], h[None])[0]
+            worst = max(worst, float(d))
             continue
         worst = max(worst, float(np.abs(s1[i] - ref).max()))
     assert n_amb <= 3
