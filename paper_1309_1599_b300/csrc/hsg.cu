@@ -829,11 +829,16 @@ hsg_status enqueue_energy(hsg_ctx* h, cudaStream_t st) {
 
 hsg_status enqueue_pt(hsg_ctx* h, cudaStream_t st) {
   const int n_sets = h->S * h->n_rep;
-  const int threads = 128;
   *h->launch_sink += 1;
-  k_pt_sweep<<<(n_sets + threads - 1) / threads, threads, 0, st>>>(
-      n_sets, h->n_rep, h->NT, h->R, h->d_beta, h->d_E, h->d_perm, h->d_temp_of, h->d_pt_acc,
-      philox_key(h->seed), h->d_counters);
+  if (h->NT <= kPtWarpMaxTemps) {
+    k_pt_sweep_warp<<<n_sets, 32, 0, st>>>(h->n_rep, h->NT, h->R, h->d_beta, h->d_E, h->d_perm, h->d_temp_of,
+                                           h->d_pt_acc, philox_key(h->seed), h->d_counters);
+  } else {
+    const int threads = 128;
+    k_pt_sweep<<<(n_sets + threads - 1) / threads, threads, 0, st>>>(
+        n_sets, h->n_rep, h->NT, h->R, h->d_beta, h->d_E, h->d_perm, h->d_temp_of, h->d_pt_acc,
+        philox_key(h->seed), h->d_counters);
+  }
   HSG_CUDA(cudaGetLastError());
   return HSG_OK;
 }

@@ -555,6 +555,66 @@ static __global__ void k_pt_sweep(int n_sets, int n_rep, int NT, int R, const do
   for (int k = 0; k < NT; ++k) temp_of[static_cast<size_t>(s) * R + pm[k]] = k;
 }
 
+// The same parallel-tempering sweep with one warp per replica set, for up to
+// kPtWarpMaxTemps temperatures: the lanes stage the set's labels, the
+// energies of the lattices they point at and the random numbers of every
+// pair in shared memory, lane 0 runs the sequential sweep over the pairs in
+// k_pt_sweep's order and arithmetic (so the decisions are the same bit for
+// bit), and the lanes write the labels and acceptances back.  The sweep no
+// longer waits on a global load per pair.
+constexpr int kPtWarpMaxTemps = 256;
+
+static __global__ void __launch_bounds__(32) k_pt_sweep_warp(int n_rep, int NT, int R,
+                                                             const double* __restrict__ beta,
+                                                             const double* __restrict__ E, int* __restrict__ perm,
+                                                             int* __restrict__ temp_of,
+                                                             long long* __restrict__ accepted, uint2 key,
+                                                             const uint32_t* __restrict__ counters) {
+  __shared__ int s_lab[kPtWarpMaxTemps];
+  __shared__ double s_en[kPtWarpMaxTemps], s_beta[kPtWarpMaxTemps], s_r[kPtWarpMaxTemps];
+  __shared__ unsigned char s_acc[kPtWarpMaxTemps];
+  const int gset = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int s = gset / n_rep;
+  int* pm = perm + static_cast<size_t>(gset) * NT;
+  const double* Es = E + static_cast<size_t>(s) * R;
+  const uint32_t t = counters[1];
+  for (int k = lane; k < NT; k += 32) {
+    const int a = pm[k];
+    s_lab[k] = a;
+    s_en[k] = Es[a];
+    s_beta[k] = beta[k];
+    s_acc[k] = 0;
+    if (k + 1 < NT) {
+      const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(gset), t,
+                                               kTagTempering), key);
+      s_r[k] = uniform52(w.x, w.y);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int k = 0; k + 1 < NT; ++k) {
+      const double delta = (s_beta[k] - s_beta[k + 1]) * (s_en[k] - s_en[k + 1]);
+      if (delta >= 0.0 || s_r[k] < exp(delta)) {
+        const int a = s_lab[k];
+        s_lab[k] = s_lab[k + 1];
+        s_lab[k + 1] = a;
+        const double e = s_en[k];
+        s_en[k] = s_en[k + 1];
+        s_en[k + 1] = e;
+        s_acc[k] = 1;
+      }
+    }
+  }
+  __syncwarp();
+  const int acc_stride = NT > 1 ? NT - 1 : 1;
+  for (int k = lane; k < NT; k += 32) {
+    pm[k] = s_lab[k];
+    temp_of[static_cast<size_t>(s) * R + s_lab[k]] = k;
+    if (s_acc[k]) accepted[static_cast<size_t>(gset) * acc_stride + k] += 1;
+  }
+}
+
 static __global__ void k_bump_counters(uint32_t* counters, uint32_t d_hb, uint32_t d_pt) {
   counters[0] += d_hb;
   counters[1] += d_pt;

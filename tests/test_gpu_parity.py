@@ -120,13 +120,16 @@ def test_ferromagnet_energies_seven_digits():
         assert -3 * L ** 3 < ref < -2.0 * L ** 3     # ordered at T = 0.5
 
 
-def test_pt_labels_bit_exact():
-    betas = gi.linear_betas(0.2, 1.5, 7)
-    lat, J = make([6, 6, 6], betas, n_rep=3)
+# 7 temperatures; 33 (a warp's lanes take two pairs each); 300 (more than the
+# warp-per-set kernel stages: the thread-per-set kernel)
+@pytest.mark.parametrize("NT,L", [(7, 6), (33, 4), (300, 4)])
+def test_pt_labels_bit_exact(NT, L):
+    betas = gi.linear_betas(0.2, 1.5, NT)
+    lat, J = make([L, L, L], betas, n_rep=3)
     rng = np.random.default_rng(4)
-    N = 216
+    N = L ** 3
     perm = lat.get_perm().copy()
-    acc = np.zeros((3, 3, 6), dtype=np.int64)
+    acc = np.zeros((3, 3, NT - 1), dtype=np.int64)
     for t in range(40):
         E = rng.normal(-1.5 * N, 0.05 * N, size=(3, lat.R))
         lat.set_energies(E)
@@ -136,7 +139,7 @@ def test_pt_labels_bit_exact():
                 oracle.pt_sweep(betas, E[s], perm[s, r], lat.seed, s * 3 + r, t, acc[s, r])
         assert np.array_equal(lat.get_perm(), perm)
     assert np.array_equal(lat.get_pt_accepts(), acc)
-    assert 0 < acc.sum() < 40 * 54
+    assert 0 < acc.sum() < 40 * acc.size
 
 
 def _oracle_measure(lat, J, st, E):
