@@ -90,26 +90,26 @@ MID_WORKLOAD = "L16_S512_R32_f16"
 FUSED_SOURCES = ("kernels.cuh", "fused.cuh", "philox.cuh")
 RESIDENT_SOURCES = ("kernels.cuh", "persistent.cuh", "philox.cuh")
 NCU_TRAFFIC = {
-    # the L=64 overrelaxation sweep in 8-row bands: 388.0 MB for one sample of
+    # the L=64 overrelaxation sweep in 8-row bands: 387.9 MB for one sample of
     # 64 lattices, x8 samples
-    ("0b00f107ce937a92", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3103889408,
-    # the same sweep of the plain FP32 form (one lattice per element): 418.4 MB
+    ("e85d062003519016", "L64_S8_R64_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 3103438848,
+    # the same sweep of the plain FP32 form (one lattice per element): 418.2 MB
     # for one sample, x8 samples; the 64 lattices of a sample read their
     # shared couplings through L2, so this is far below the 96 B per update
     # that lattices with couplings of their own move
-    ("0b00f107ce937a92", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3347093504,
+    ("e85d062003519016", "L64_S8_R64_f16", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 3345754112,
     # the plain single-lattice form (FP32 couplings of its own per lattice):
-    # 365.0 MB read + 42.6 MB written for 16 lattices (97.2 B per update
+    # 365.0 MB read + 42.2 MB written for 16 lattices (97.1 B per update
     # against the algorithmic 96), x32 for the 512 lattices timed beside the
     # default workload
-    ("0b00f107ce937a92", "L64_S16_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 407521536,
-    ("0b00f107ce937a92", "L64_S512_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 13040689152,
+    ("e85d062003519016", "L64_S16_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 407172608,
+    ("e85d062003519016", "L64_S512_R1_f32_plain", "k_sweep_fused<OR,1,f32> (bands of 8 rows)"): 13029523456,
     # the L=32 overrelaxation sweep: one launch of 64 samples x 48 lattices
-    ("0b00f107ce937a92", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2645652480,
+    ("e85d062003519016", "L32_S64_R48_f16", "k_sweep_fused<OR,2,f16> (bands of 8 rows)"): 2644966144,
     # the resident steps of 256 x L=8 + 256 x L=12 samples, both sizes in one
-    # launch of 10 MCS: 249.5 MB read + 164.2 MB written
-    ("f136a483a416a5be", "L8x256_L12x256_R32_f16",
-     "k_persistent_pair<2,f16> (10 MCS per launch, both lattice sizes in one launch)"): 413778688,
+    # launch of 10 MCS: 249.3 MB read + 163.8 MB written
+    ("629648d1f094eef9", "L8x256_L12x256_R32_f16",
+     "k_persistent_pair<2,f16> (10 MCS per launch, both lattice sizes in one launch)"): 413147648,
 }
 
 
